@@ -1,0 +1,195 @@
+/*
+ * styleblit.h -- C ABI of the GB300 (sm_103a) StyleBlit library.
+ *
+ * StyleBlit (Sykora, Jamriska, Lu, Shechtman, "StyleBlit: Fast Example-Based
+ * Stylization with Local Guidance", EGSR 2018) stylises a target image from a
+ * style exemplar by copying translated chunks of the exemplar.  Its problem
+ * statement (inputs of Algorithms 1 and 2): a source style exemplar C_S, source
+ * guides G_S, target guides G_T, a threshold t and a number of levels L; the
+ * output is the stylised target C_T.
+ *
+ * Conventions shared by every entry point
+ *   - Image pointers are DEVICE pointers owned by the caller.  Inputs are only
+ *     read; outputs are fully overwritten on success and left unspecified on
+ *     error (no partial-output guarantee).
+ *   - Guides are interleaved HWC.  8-bit guides may have 1..4 channels, 16-bit
+ *     guides 1..2 channels (16-bit samples little-endian, rows 2-byte aligned).
+ *     Target and source guides must have the same channel count and depth.
+ *   - Styles are RGBA8, interleaved, rows 4-byte aligned.
+ *   - Sizes: 1 <= source width/height <= 32767 (positions are packed into 16
+ *     bits each; the extra bit keeps packed-position arithmetic carry-free);
+ *     target width/height <= 65535, zero-sized targets are a no-op.
+ *   - Source positions are packed as x | y << 16 in a uint32.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
+ *     call only enqueues work on `stream` and returns without synchronising;
+ *     results are ready when the stream reaches that point.
+ *   - Every call returns SB_OK (0) or a negative sb_status.  Arguments are
+ *     validated on the host before anything is launched; sb_last_error()
+ *     returns a message for the most recent failure on the calling thread.
+ *   - The library owns sb_lut objects (created by sb_build_lut, freed by
+ *     sb_lut_destroy); it allocates device memory only inside sb_build_lut.
+ *
+ * The reading of the paper this library computes (shared with its CPU
+ * oracle): the level loop of Algorithm 2 with seed spacing 2^l for l = L..1,
+ * seeds jittered by a hash of (seed, level, cell) and clamped into the
+ * target, nearest seed over the 3 x 3 neighbouring cells (x outer, y inner,
+ * strict <), candidate u*(q) + (p - q) accepted when it lies in the source and
+ * its squared guide distance to G_T[p] is <= threshold, the finest level always
+ * accepting (candidate clamped into the source); then the voting step of
+ * Section 3.2 over a (2r+1) x (2r+1) window with integer sums and round-half-up
+ * division.
+ */
+#ifndef STYLEBLIT_H
+#define STYLEBLIT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SB_API __attribute__((visibility("default")))
+#else
+#define SB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SB_OK = 0,
+    SB_ERR_INVALID_ARG = -1,   /* a pointer, size or parameter is out of range */
+    SB_ERR_UNSUPPORTED = -2,   /* a valid request this build does not implement */
+    SB_ERR_CUDA = -3,          /* a CUDA call failed (sticky errors included) */
+    SB_ERR_OOM = -4,           /* device allocation failed */
+    SB_ERR_TIMEOUT = -5        /* a bounded device-side wait gave up */
+} sb_status;
+
+typedef void *sb_stream;       /* cudaStream_t */
+
+/* A guide image G_S or G_T (device memory, interleaved HWC). */
+typedef struct {
+    const void *data;
+    int32_t width;
+    int32_t height;
+    int32_t channels;          /* 1..4 for 8-bit, 1..2 for 16-bit */
+    int32_t bits;              /* 8 or 16 */
+    int64_t row_stride;        /* bytes between row starts, >= width*channels*bits/8 */
+} sb_guide;
+
+/* A style exemplar C_S (device memory, RGBA8). */
+typedef struct {
+    const uint8_t *data;
+    int32_t width;
+    int32_t height;
+    int64_t row_stride;        /* bytes, multiple of 4, >= 4*width */
+} sb_rgba8;
+
+/* Opaque, library-owned guide look-up table of one exemplar. */
+typedef struct sb_lut sb_lut;
+
+/*
+ * sb_build_lut -- the guide look-up table of Section 3.1.
+ *
+ * The paper notes that the local guide (usually two values) indirectly names
+ * a source position, so a look-up table can return, for a target guide value,
+ * the source pixel with the nearest guide (u* = argmin_u ||G_T[q] - G_S[u]||
+ * in Algorithm 2, "found via lookup").  The table quantises each guide
+ * channel to its top `key_bits` bits; bin k (channel keys concatenated,
+ * channel 0 lowest) maps to the source pixel minimising the squared guide
+ * distance to the bin representative rep_c = (key_c << z) + ((2^z - 1) >> 1),
+ * z = bits - key_bits, ties to the smallest y * width + x.  The search is
+ * exact (a pruned brute-force nearest-neighbour kernel).
+ *
+ *   src_guide  source guide G_S (device).  The table refers to positions in
+ *              it; later calls must pass a source guide of the same size and
+ *              format (checked) and the same content (not checked).
+ *   key_bits   bits kept per channel, 1 <= key_bits <= bits and
+ *              channels * key_bits <= 24 (at most 16 Mi entries, 64 MiB).
+ *   out        receives the new table; untouched on error.
+ *   stream     the build is enqueued on this stream.  Temporary device
+ *              memory is allocated and freed inside the call (stream-ordered).
+ * Errors: SB_ERR_INVALID_ARG, SB_ERR_UNSUPPORTED, SB_ERR_OOM, SB_ERR_CUDA.
+ */
+SB_API sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, sb_lut **out,
+                       sb_stream stream);
+
+/* Frees a table (NULL is a no-op).  The caller must ensure no enqueued work
+ * still uses it (e.g. synchronise the streams that used it first). */
+SB_API sb_status sb_lut_destroy(sb_lut *lut);
+
+/* Describes a table: device pointer to its 2^(channels*key_bits) uint32
+ * entries (packed x | y << 16), entry count, channels, bits and key_bits of
+ * the guide it was built for, and that guide's width and height.  Any output
+ * pointer may be NULL. */
+SB_API sb_status sb_lut_info(const sb_lut *lut, const uint32_t **entries, int64_t *n_entries,
+                      int32_t *channels, int32_t *bits, int32_t *key_bits,
+                      int32_t *src_width, int32_t *src_height);
+
+/*
+ * sb_assign_chunks -- Algorithm 2 (ParallelStyleBlit) with coordinate
+ * transfer (Section 3.2): the source position every target pixel copies from.
+ *
+ *   tgt_guide   target guide G_T (device).
+ *   src_guide   source guide G_S (device), the one `lut` was built from.
+ *   lut         table from sb_build_lut for src_guide.
+ *   levels      L, 1 <= L <= 12; level l uses seed spacing 2^l.
+ *   threshold   t, compared as squared integer guide distance (<=).
+ *   seed        frame seed of the jitter hash (re-randomise per frame for
+ *               the controllable flicker of Section 3.3).
+ *   assign_out  device uint32[tgt h * tgt w], row-major: A(p) = x | y << 16.
+ *   level_out   device uint8[tgt h * tgt w]: the level that accepted p, or
+ *               NULL.
+ * Errors: SB_ERR_INVALID_ARG, SB_ERR_UNSUPPORTED, SB_ERR_CUDA.
+ */
+SB_API sb_status sb_assign_chunks(const sb_guide *tgt_guide, const sb_guide *src_guide,
+                           const sb_lut *lut, int32_t levels, uint64_t threshold,
+                           uint32_t seed, uint32_t *assign_out, uint8_t *level_out,
+                           sb_stream stream);
+
+/*
+ * sb_blend -- the voting step of Section 3.2: the colour of p is the average
+ * of C_S[A(p + o) - o] over the window offsets o in [-r, r]^2 whose p + o lies
+ * in the target and whose A(p + o) - o lies in the source.
+ *
+ *   assign        device uint32[tgt_h * tgt_w] from sb_assign_chunks.
+ *   src_style     C_S (device).  Every A(p) must lie inside it.
+ *   blend_radius  r, 0 <= r <= 15 (r = 0 copies C_S[A(p)]).
+ *   rgba8_out     device uint8[tgt_h * tgt_w * 4]: (sum + n/2) / n, or
+ *   rgba32f_out   device float[tgt_h * tgt_w * 4]: sum / (255 n).
+ *                 Exactly one of the two outputs must be non-NULL.
+ * Errors: SB_ERR_INVALID_ARG, SB_ERR_CUDA.
+ */
+SB_API sb_status sb_blend(const uint32_t *assign, int32_t tgt_w, int32_t tgt_h,
+                   const sb_rgba8 *src_style, int32_t blend_radius, uint8_t *rgba8_out,
+                   float *rgba32f_out, sb_stream stream);
+
+/*
+ * sb_stylize -- assignment and voting fused in one kernel (Algorithm 2 plus
+ * the voting step of Section 3.2); the assignment map never reaches device
+ * memory.  Bit-identical to sb_assign_chunks followed by sb_blend(rgba8).
+ *
+ *   tgt_guide, src_guide, lut, levels, threshold, seed: as sb_assign_chunks.
+ *   src_style     C_S (device), same width and height as src_guide.
+ *   blend_radius  r, 0 <= r <= 7.
+ *   rgba8_out     device uint8[tgt h * tgt w * 4] (row-major, tightly packed).
+ * Errors: SB_ERR_INVALID_ARG, SB_ERR_UNSUPPORTED, SB_ERR_CUDA.
+ */
+SB_API sb_status sb_stylize(const sb_guide *tgt_guide, const sb_guide *src_guide,
+                     const sb_rgba8 *src_style, const sb_lut *lut, int32_t levels,
+                     uint64_t threshold, int32_t blend_radius, uint32_t seed,
+                     uint8_t *rgba8_out, sb_stream stream);
+
+/* Static description of a status code. */
+SB_API const char *sb_status_string(sb_status status);
+
+/* Message describing the most recent failure on the calling thread ("" if
+ * none).  The pointer stays valid until the next library call on the thread. */
+SB_API const char *sb_last_error(void);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+SB_API int32_t sb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STYLEBLIT_H */

@@ -1,0 +1,253 @@
+// Guide look-up table of StyleBlit (Section 3.1: the local guide names a
+// source position, so a look-up table returns, for a guide value, the source
+// pixel with the nearest guide; Algorithm 2 calls this lookup for u*).
+//
+// The table is exact: bin k maps to argmin_u |rep(k) - G_S[u]|^2 with ties to
+// the smallest linear index.  Two kernels:
+//   1. lut_tile_bounds: per 16x16 source tile, the per-channel min/max of the
+//      guide (an axis-aligned box in guide space).
+//   2. lut_search: one thread per bin, bins enumerated in Morton order so a
+//      warp covers a compact box of guide space.  Each lane first scans the
+//      tile whose box is nearest to its representative, then the warp walks
+//      every tile and scans it only if some lane's box distance can still
+//      beat (or tie with a smaller index) that lane's best.  A skipped tile
+//      holds no pixel strictly closer than the best and no tie with a smaller
+//      linear index, so the result equals the brute-force argmin.
+#include <algorithm>
+#include <cstdio>
+
+#include "sb_internal.cuh"
+
+namespace sb {
+
+constexpr int kLutTile = 16;
+constexpr int kLutThreads = 256;
+
+template <int C, int B>
+__global__ void __launch_bounds__(256) lut_tile_bounds_kernel(const uint8_t *__restrict__ src,
+                                                              int64_t stride, int W, int H,
+                                                              int tiles_x, int n_tiles,
+                                                              uint4 *__restrict__ bounds) {
+    using F = GuideFmt<C, B>;
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= n_tiles) return;  // whole warps exit together
+    const int x0 = (warp % tiles_x) * kLutTile;
+    const int y0 = (warp / tiles_x) * kLutTile;
+    uint32_t mn[C], mx[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        mn[c] = 0xFFFFu;
+        mx[c] = 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kLutTile * kLutTile / 32; ++k) {
+        const int i = lane + 32 * k;
+        const int x = x0 + (i % kLutTile), y = y0 + (i / kLutTile);
+        if (x < W && y < H) {
+            const uint32_t v = F::load(src, stride, x, y);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                mn[c] = min(mn[c], F::chan(v, c));
+                mx[c] = max(mx[c], F::chan(v, c));
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            mn[c] = min(mn[c], __shfl_xor_sync(0xFFFFFFFFu, mn[c], off));
+            mx[c] = max(mx[c], __shfl_xor_sync(0xFFFFFFFFu, mx[c], off));
+        }
+    }
+    if (lane == 0) {
+        uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < C; ++c) w[c] = mn[c] | (mx[c] << 16);
+        bounds[warp] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// squared distance from a representative to a tile's guide box
+template <int C, int B>
+__device__ __forceinline__ uint64_t box_distance(const uint32_t (&rep)[C], uint4 bb) {
+    const uint32_t w[4] = {bb.x, bb.y, bb.z, bb.w};
+    uint64_t lb = 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const uint32_t lo = w[c] & 0xFFFFu, hi = w[c] >> 16;
+        const uint32_t t = rep[c] < lo ? lo - rep[c] : (rep[c] > hi ? rep[c] - hi : 0u);
+        lb += (uint64_t)t * t;
+    }
+    return lb;
+}
+
+template <int C, int B>
+__device__ __forceinline__ void scan_tile(const uint8_t *__restrict__ src, int64_t stride, int W,
+                                          int H, int tiles_x, int t, uint32_t rep_packed,
+                                          uint64_t &bd, uint32_t &bl) {
+    using F = GuideFmt<C, B>;
+    const int x0 = (t % tiles_x) * kLutTile;
+    const int y0 = (t / tiles_x) * kLutTile;
+    const int x1 = min(x0 + kLutTile, W), y1 = min(y0 + kLutTile, H);
+    for (int y = y0; y < y1; ++y) {
+#pragma unroll 4
+        for (int x = x0; x < x1; ++x) {
+            const uint64_t d = F::dist(rep_packed, F::load(src, stride, x, y));
+            const uint32_t lin = (uint32_t)y * (uint32_t)W + (uint32_t)x;
+            if (d < bd || (d == bd && lin < bl)) {
+                bd = d;
+                bl = lin;
+            }
+        }
+    }
+}
+
+template <int C, int B>
+__global__ void __launch_bounds__(kLutThreads)
+    lut_search_kernel(const uint8_t *__restrict__ src, int64_t stride, int W, int H, int tiles_x,
+                      int n_tiles, const uint4 *__restrict__ bounds, int key_bits,
+                      uint32_t n_bins, uint32_t *__restrict__ lut) {
+    using F = GuideFmt<C, B>;
+    const uint32_t g = blockIdx.x * kLutThreads + threadIdx.x;
+    const bool valid = g < n_bins;
+
+    // Morton order: bit i of g is bit i / C of channel i % C's key
+    uint32_t key[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) key[c] = 0;
+    for (int i = 0; i < C * key_bits; ++i) key[i % C] |= ((g >> i) & 1u) << (i / C);
+    const int z = B - key_bits;
+    uint32_t rep[C];
+    uint32_t rep_packed = 0, idx = 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        rep[c] = (key[c] << z) + (((1u << z) - 1u) >> 1);
+        rep_packed |= rep[c] << (c * B);
+        idx |= key[c] << (c * key_bits);
+    }
+
+    // pass A: the tile whose guide box is nearest
+    uint64_t best_lb = ~0ull;
+    int best_t = 0;
+    for (int t = 0; t < n_tiles; ++t) {
+        const uint64_t lb = box_distance<C, B>(rep, __ldg(&bounds[t]));
+        if (lb < best_lb) {
+            best_lb = lb;
+            best_t = t;
+        }
+    }
+    // pass B: an initial best from that tile
+    uint64_t bd = ~0ull;
+    uint32_t bl = 0xFFFFFFFFu;
+    scan_tile<C, B>(src, stride, W, H, tiles_x, best_t, rep_packed, bd, bl);
+    // pass C: every tile that could still hold a better or tied-earlier pixel
+    for (int t = 0; t < n_tiles; ++t) {
+        const uint64_t lb = box_distance<C, B>(rep, __ldg(&bounds[t]));
+        const uint32_t first = (uint32_t)((t / tiles_x) * kLutTile) * (uint32_t)W +
+                               (uint32_t)((t % tiles_x) * kLutTile);
+        const bool need = valid && (lb < bd || (lb == bd && first < bl));
+        if (__any_sync(0xFFFFFFFFu, need))
+            scan_tile<C, B>(src, stride, W, H, tiles_x, t, rep_packed, bd, bl);
+    }
+    if (valid) lut[idx] = (bl % (uint32_t)W) | ((bl / (uint32_t)W) << 16);
+}
+
+struct LutLaunch {
+    const sb_guide *src;
+    int key_bits;
+    uint32_t n_bins;
+    uint4 *bounds;
+    uint32_t *entries;
+    cudaStream_t stream;
+    template <int C, int B>
+    void operator()() {
+        const int tiles_x = (src->width + kLutTile - 1) / kLutTile;
+        const int tiles_y = (src->height + kLutTile - 1) / kLutTile;
+        const int n_tiles = tiles_x * tiles_y;
+        const uint8_t *p = static_cast<const uint8_t *>(src->data);
+        lut_tile_bounds_kernel<C, B><<<(n_tiles + 7) / 8, 256, 0, stream>>>(
+            p, src->row_stride, src->width, src->height, tiles_x, n_tiles, bounds);
+        lut_search_kernel<C, B><<<(n_bins + kLutThreads - 1) / kLutThreads, kLutThreads, 0,
+                                  stream>>>(p, src->row_stride, src->width, src->height,
+                                            tiles_x, n_tiles, bounds, key_bits, n_bins,
+                                            entries);
+    }
+};
+
+}  // namespace sb
+
+using namespace sb;
+
+extern "C" sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, sb_lut **out,
+                                  sb_stream stream) {
+    sb_status st = check_guide(src_guide, "src_guide", true);
+    if (st != SB_OK) return st;
+    if (!out) return fail(SB_ERR_INVALID_ARG, "out: NULL");
+    if (key_bits < 1 || key_bits > src_guide->bits)
+        return fail(SB_ERR_INVALID_ARG, "key_bits must be in [1, bits]");
+    if (src_guide->channels * key_bits > kMaxKeyBitsTotal)
+        return fail(SB_ERR_INVALID_ARG, "channels * key_bits must be <= 24");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "sb_build_lut: pending CUDA error");
+
+    const uint32_t n_bins = 1u << (src_guide->channels * key_bits);
+    const int tiles_x = (src_guide->width + kLutTile - 1) / kLutTile;
+    const int tiles_y = (src_guide->height + kLutTile - 1) / kLutTile;
+    const size_t n_tiles = (size_t)tiles_x * tiles_y;
+
+    sb_lut *lut = new sb_lut;
+    lut->n_entries = n_bins;
+    lut->channels = src_guide->channels;
+    lut->bits = src_guide->bits;
+    lut->key_bits = key_bits;
+    lut->src_w = src_guide->width;
+    lut->src_h = src_guide->height;
+    cudaGetDevice(&lut->device);
+    if ((e = cudaMalloc(&lut->entries, sizeof(uint32_t) * n_bins)) != cudaSuccess) {
+        delete lut;
+        return cuda_fail(e, "sb_build_lut: table allocation");
+    }
+    uint4 *bounds = nullptr;
+    if ((e = cudaMallocAsync(&bounds, sizeof(uint4) * n_tiles, s)) != cudaSuccess) {
+        cudaFree(lut->entries);
+        delete lut;
+        return cuda_fail(e, "sb_build_lut: scratch allocation");
+    }
+    LutLaunch L{src_guide, key_bits, n_bins, bounds, lut->entries, s};
+    dispatch_format(src_guide->channels, src_guide->bits, L);
+    e = cudaGetLastError();
+    cudaFreeAsync(bounds, s);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        cudaFree(lut->entries);
+        delete lut;
+        return cuda_fail(e, "sb_build_lut: launch");
+    }
+    *out = lut;
+    return ok();
+}
+
+extern "C" sb_status sb_lut_destroy(sb_lut *lut) {
+    if (!lut) return ok();
+    cudaError_t e = cudaFree(lut->entries);
+    delete lut;
+    if (e != cudaSuccess) return cuda_fail(e, "sb_lut_destroy");
+    return ok();
+}
+
+extern "C" sb_status sb_lut_info(const sb_lut *lut, const uint32_t **entries, int64_t *n_entries,
+                                 int32_t *channels, int32_t *bits, int32_t *key_bits,
+                                 int32_t *src_width, int32_t *src_height) {
+    if (!lut) return fail(SB_ERR_INVALID_ARG, "lut: NULL");
+    if (entries) *entries = lut->entries;
+    if (n_entries) *n_entries = lut->n_entries;
+    if (channels) *channels = lut->channels;
+    if (bits) *bits = lut->bits;
+    if (key_bits) *key_bits = lut->key_bits;
+    if (src_width) *src_width = lut->src_w;
+    if (src_height) *src_height = lut->src_h;
+    return ok();
+}

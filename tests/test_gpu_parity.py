@@ -1,0 +1,226 @@
+"""Parity of the CUDA library (through its C ABI) with the CPU oracle.
+
+The bar is bit-exactness: look-up tables, assignment maps, level maps and
+RGBA8 outputs are integer results and must equal the oracle's element by
+element; the float vote must be within 1e-5 absolute.  Small cases compare
+whole frames; the 1920x1080 and 3840x2160 workloads compare sampled pixels
+(the oracle computes each one from scratch) and check full-frame properties.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1807_03249_gb300 as sb
+import synth
+from tests.gpu_helpers import sample_pixels, to_dev, u32, workload
+from tests.golden.cases import REGRESSION_CASES, make_case
+
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-5
+
+
+def _full(dev, c, radius=None):
+    radius = c["radius"] if radius is None else radius
+    gt, gs, st = to_dev(c["tgt"], dev), to_dev(c["src"], dev), to_dev(c["style"], dev)
+    lut = sb.build_lut(gs, c["key_bits"])
+    a, lev = sb.assign_chunks(gt, gs, lut, c["levels"], c["threshold"], c["seed"])
+    out = sb.stylize(gt, gs, st, lut, c["levels"], c["threshold"], radius, c["seed"])
+    torch.cuda.synchronize()
+    return lut, u32(a), lev.cpu().numpy(), out.cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+# look-up table (Section 3.1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("channels,bits,key_bits,shape", [
+    (3, 8, 4, (37, 45)), (2, 8, 6, (64, 64)), (1, 8, 8, (17, 9)), (4, 8, 3, (33, 20)),
+    (2, 16, 7, (48, 40)), (1, 16, 10, (30, 31)), (3, 8, 5, (1, 1)), (2, 8, 8, (70, 3))])
+def test_lut_all_entries_match_oracle(cuda_device, channels, bits, key_bits, shape):
+    H, W = shape
+    src = synth.random_guide(1000 + channels * 7 + bits, H, W, channels, bits=bits)
+    lut = sb.build_lut(to_dev(src, cuda_device), key_bits)
+    got = lut.entries().cpu().numpy().view(np.uint32)
+    ref = oracle.build_lut(src, key_bits)
+    assert np.array_equal(got, ref)
+
+
+def test_lut_with_ties_and_constant_regions(cuda_device):
+    src = synth.random_guide(5, 50, 41, 2, bits=8, low=100, high=103)  # heavy ties
+    src[10:30, 5:25] = 7
+    lut = sb.build_lut(to_dev(src, cuda_device), 5)
+    assert np.array_equal(lut.entries().cpu().numpy().view(np.uint32),
+                          oracle.build_lut(src, 5))
+
+
+def test_lut_sphere_normals_full_table(cuda_device):
+    src = synth.sphere_normals(128)
+    lut = sb.build_lut(to_dev(src, cuda_device), 5)
+    assert np.array_equal(lut.entries().cpu().numpy().view(np.uint32),
+                          oracle.build_lut(src, 5))
+
+
+@pytest.mark.parametrize("name", ["1080p", "4k"])
+def test_lut_full_size_sampled_bins(cuda_device, name):
+    w = workload(name)
+    ex = w.exemplar
+    lut = sb.build_lut(to_dev(ex.guide, cuda_device), ex.lut_bits)
+    got = lut.entries().cpu().numpy().view(np.uint32)
+    assert got.shape[0] == 1 << (ex.guide.shape[2] * ex.lut_bits)
+    rng = np.random.default_rng(7)
+    idx = np.concatenate([rng.integers(0, got.shape[0], 160), [0, got.shape[0] - 1]])
+    assert np.array_equal(got[idx], oracle.lut_entries(ex.guide, ex.lut_bits, idx))
+    # every entry is a valid source position
+    assert ((got & 0xFFFF) < ex.guide.shape[1]).all() and ((got >> 16) < ex.guide.shape[0]).all()
+
+
+# ---------------------------------------------------------------------------
+# assignment (Algorithm 2) and fused stylisation, whole small frames
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", REGRESSION_CASES)
+def test_small_cases_bit_exact(cuda_device, name):
+    c = make_case(name)
+    lut, a, lev, out = _full(cuda_device, c)
+    ref_out, ref_a, ref_lev = oracle.stylize(c["tgt"], c["src"], c["style"], c["key_bits"],
+                                             c["levels"], c["threshold"], c["radius"], c["seed"])
+    assert np.array_equal(a, ref_a)
+    assert np.array_equal(lev, ref_lev)
+    assert np.array_equal(out, ref_out)
+
+
+@pytest.mark.parametrize("radius", [0, 1, 2, 3, 5, 7])
+def test_workload_256_every_radius(cuda_device, radius):
+    w = workload("256")
+    ex, fr = w.exemplar, w.frames[0]
+    c = dict(tgt=fr.guide, src=ex.guide, style=ex.style, key_bits=ex.lut_bits,
+             levels=w.levels, threshold=w.threshold, radius=radius, seed=w.seed)
+    lut, a, lev, out = _full(cuda_device, c)
+    ref_out, ref_a, ref_lev = oracle.stylize(fr.guide, ex.guide, ex.style, ex.lut_bits, w.levels,
+                                             w.threshold, radius, w.seed, n_threads=4)
+    assert np.array_equal(a, ref_a) and np.array_equal(lev, ref_lev)
+    assert np.array_equal(out, ref_out)
+
+
+@pytest.mark.parametrize("shape,levels,T,seed", [
+    ((1, 1), 3, 100, 0), ((1, 97), 4, 50, 1), ((65, 1), 2, 50, 2), ((33, 65), 5, 0, 3),
+    ((129, 70), 1, 100, 4), ((70, 129), 12, 200, 5), ((100, 190), 6, (1 << 64) - 1, 6),
+    ((64, 32), 7, 400, 0xFFFFFFFF), ((31, 200), 3, 300, 12345)])
+def test_ragged_and_extreme_parameters(cuda_device, shape, levels, T, seed):
+    H, W = shape
+    tgt = synth.smooth_integer_guide(seed % 1000 + 1, H, W, 3, step=5)
+    src = synth.smooth_integer_guide(seed % 1000 + 2, 40, 52, 3, step=5)
+    style = synth.random_style(seed % 1000 + 3, 40, 52)
+    c = dict(tgt=tgt, src=src, style=style, key_bits=5, levels=levels, threshold=T, radius=2,
+             seed=seed)
+    lut, a, lev, out = _full(cuda_device, c)
+    ref_out, ref_a, ref_lev = oracle.stylize(tgt, src, style, 5, levels, T, 2, seed)
+    assert np.array_equal(a, ref_a) and np.array_equal(lev, ref_lev)
+    assert np.array_equal(out, ref_out)
+
+
+def test_empty_targets_are_a_no_op(cuda_device):
+    src = synth.random_guide(1, 16, 16, 3)
+    gs = to_dev(src, cuda_device)
+    st = to_dev(synth.random_style(2, 16, 16), cuda_device)
+    lut = sb.build_lut(gs, 4)
+    for shape in [(0, 0, 3), (0, 9, 3), (9, 0, 3)]:
+        gt = torch.zeros(shape, dtype=torch.uint8, device=cuda_device)
+        out = sb.stylize(gt, gs, st, lut, 3, 100, 2, 0)
+        a, lev = sb.assign_chunks(gt, gs, lut, 3, 100, 0)
+        assert out.numel() == 0 and a.numel() == 0
+    torch.cuda.synchronize()
+
+
+def test_identity_uv_reproduces_the_exemplar(cuda_device):
+    H, W = 200, 300
+    g = synth.identity_uv_guide(H, W)
+    style = synth.random_style(9, H, W)
+    gd = to_dev(g, cuda_device)
+    st = to_dev(style, cuda_device)
+    lut = sb.build_lut(gd, 11)
+    for radius in (0, 3, 7):
+        out = sb.stylize(gd, gd, st, lut, 6, 0, radius, 77)
+        assert np.array_equal(out.cpu().numpy(), style)
+    a, lev = sb.assign_chunks(gd, gd, lut, 6, 0, 77)
+    ys, xs = np.mgrid[0:H, 0:W]
+    A = u32(a)
+    assert np.array_equal(A & 0xFFFF, xs) and np.array_equal(A >> 16, ys)
+    assert (lev.cpu().numpy() == 6).all()
+
+
+def test_unused_style_rows_and_strided_guides(cuda_device):
+    """Row strides larger than the row (a crop of a bigger buffer)."""
+    c = make_case("u8x2-33x29-L4-T60-r2")
+    big_t = np.zeros((c["tgt"].shape[0], c["tgt"].shape[1] + 7, 2), dtype=np.uint8)
+    big_t[:, :c["tgt"].shape[1]] = c["tgt"]
+    big_s = np.zeros((c["style"].shape[0], c["style"].shape[1] + 3, 4), dtype=np.uint8)
+    big_s[:, :c["style"].shape[1]] = c["style"]
+    gt = to_dev(big_t, cuda_device)[:, :c["tgt"].shape[1]]
+    gs = to_dev(c["src"], cuda_device)
+    st = to_dev(big_s, cuda_device)[:, :c["style"].shape[1]]
+    lut = sb.build_lut(gs, c["key_bits"])
+    out = sb.stylize(gt, gs, st, lut, c["levels"], c["threshold"], c["radius"], c["seed"])
+    ref_out, _, _ = oracle.stylize(c["tgt"], c["src"], c["style"], c["key_bits"], c["levels"],
+                                   c["threshold"], c["radius"], c["seed"])
+    assert np.array_equal(out.cpu().numpy(), ref_out)
+
+
+# ---------------------------------------------------------------------------
+# voting (Section 3.2) from oracle assignment maps
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("radius", [0, 1, 2, 3, 7, 11, 15])
+def test_blend_rgba8_and_f32_match_oracle(cuda_device, radius):
+    w = workload("256")
+    ex, fr = w.exemplar, w.frames[0]
+    a, _ = oracle.assign(fr.guide, ex.guide, ex.lut_bits, w.levels, 60, w.seed, n_threads=4)
+    a = a[:150, :201]  # ragged
+    ad = torch.from_numpy(a.view(np.int32).copy()).to(cuda_device)
+    st = to_dev(ex.style, cuda_device)
+    out8 = sb.blend(ad, st, radius)
+    outf = sb.blend(ad, st, radius, f32=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(out8.cpu().numpy(), oracle.blend_rgba8(a, ex.style, radius))
+    ref = oracle.blend_f32(a, ex.style, radius)
+    assert np.abs(outf.cpu().numpy().astype(np.float64) - ref).max() <= F32_TOL
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads: sampled pixels and full-frame properties
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["1080p", "4k"])
+def test_full_size_sampled_parity_and_properties(cuda_device, name):
+    w = workload(name)
+    ex, fr = w.exemplar, w.frames[0]
+    H, W = fr.guide.shape[:2]
+    gt, gs, st = (to_dev(fr.guide, cuda_device), to_dev(ex.guide, cuda_device),
+                  to_dev(ex.style, cuda_device))
+    lut = sb.build_lut(gs, ex.lut_bits)
+    out = sb.stylize(gt, gs, st, lut, w.levels, w.threshold, w.blend_radius, w.seed)
+    a, lev = sb.assign_chunks(gt, gs, lut, w.levels, w.threshold, w.seed)
+    out2 = sb.blend(a, st, w.blend_radius)
+    torch.cuda.synchronize()
+    out, A, lev, out2 = out.cpu().numpy(), u32(a), lev.cpu().numpy(), out2.cpu().numpy()
+    # fused == unfused on every pixel
+    assert np.array_equal(out, out2)
+    # sampled pixels against the oracle, each computed from scratch
+    xs, ys = sample_pixels(11, W, H, 120, w.blend_radius)
+    ref_lut = oracle.new_lut(ex.guide.shape[2], ex.lut_bits)
+    ra, rl = oracle.assign_points(fr.guide, ex.guide, ex.lut_bits, w.levels, w.threshold, w.seed,
+                                  xs, ys, lut=ref_lut)
+    assert np.array_equal(A[ys, xs], ra)
+    assert np.array_equal(lev[ys, xs], rl)
+    k = 60
+    ro = oracle.stylize_points(fr.guide, ex.guide, ex.style, ex.lut_bits, w.levels, w.threshold,
+                               w.blend_radius, w.seed, xs[:k], ys[:k], lut=ref_lut)
+    assert np.array_equal(out[ys[:k], xs[:k]], ro)
+    # every accepted candidate above level 1 satisfies the threshold
+    Ax, Ay = (A & 0xFFFF).astype(np.int64), (A >> 16).astype(np.int64)
+    assert (Ax < ex.guide.shape[1]).all() and (Ay < ex.guide.shape[0]).all()
+    d = ((ex.guide[Ay, Ax].astype(np.int64) - fr.guide.astype(np.int64)) ** 2).sum(-1)
+    assert (d[lev > 1] <= w.threshold).all()
+    assert lev.min() >= 1 and lev.max() <= w.levels
