@@ -145,7 +145,7 @@ class _DeviceArray:
     """A library-owned int32 device array exposed through __cuda_array_interface__."""
 
     def __init__(self, ptr: int, n: int):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (ptr, True),
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (ptr, False),
                                          "version": 2}
 
 

@@ -3,27 +3,30 @@
 //
 // One CTA owns a 64 x 32 output tile.  For the fused path it computes the
 // assignment A of the tile plus a halo of r pixels (the vote window) in shared
-// memory, so A never touches device memory:
+// memory, so A never touches device memory.  The work is arranged so every
+// thread keeps several independent global loads in flight (the method is a
+// chain of gathers: G_T[q] -> table -> G_S[s] -> C_S[...]):
 //
-//   phase 0  target guide of the region -> smem (one packed uint32 per pixel);
-//            every in-target pixel joins the pending list.
-//   levels   for l = L..1 while pixels are pending:
-//              - the seed cells of level l that touch the region are built
-//                once per CTA: jitter hash -> seed q (clamped into the target)
-//                -> G_T[q] -> table lookup u*(q); each cell keeps
-//                (-2 q, |q|^2, u*) in region-centred coordinates;
-//              - every pending pixel takes the nearest seed of its 3 x 3 cells
-//                (x outer, y inner, strict <) by minimising |q|^2 - 2 q.p,
-//                which orders seeds exactly like |q - p|^2; it forms the
-//                candidate s = u* + (p - q) and accepts it when s lies in the
-//                source and |G_S[s] - G_T[p]|^2 <= t; level 1 always accepts
-//                (s clamped into the source); rejected pixels are compacted
-//                into the next pending list (no divergence across levels).
+//   phase 0  target guide of the region -> smem (one packed uint32 per
+//            pixel), issued as independent loads; at the same time the seed
+//            cells of all levels >= 3 are built (levels 2 and 1, which have
+//            many cells, are built only if a pixel still needs them).  A cell
+//            is: jitter hash -> seed q clamped into the target -> G_T[q] ->
+//            table lookup u*(q); it keeps (-2 q, |q|^2, u*) in region-centred
+//            coordinates.
+//   levels   for l = L..1 while pixels are pending: every pending pixel takes
+//            the nearest seed of its 3 x 3 cells (x outer, y inner, strict <)
+//            by minimising |q|^2 - 2 q.p, which orders seeds exactly like
+//            |q - p|^2; it forms s = u* + (p - q) and accepts it when s lies in
+//            the source and |G_S[s] - G_T[p]|^2 <= t (level 1 always accepts,
+//            s clamped into the source).  Pixels are processed in batches of
+//            four per thread, gathers issued before any result is used;
+//            rejected pixels are compacted into the next pending list.
 //   vote     a window whose A values are all one translation of p (checked
 //            separably: rows, then columns) votes C_S[A(p)] exactly, so it is
 //            a plain copy; the other pixels (chunk boundaries, frame borders)
-//            are compacted into a list and summed over the full window with
-//            integer sums and round-half-up division.
+//            are compacted and summed over the full window (unrolled per
+//            radius) with integer sums and round-half-up division.
 //   store    the tile leaves shared memory with coalesced 32-bit stores.
 #include <atomic>
 #include <climits>
@@ -36,6 +39,9 @@ namespace sb {
 constexpr int kTW = 64;
 constexpr int kTH = 32;
 constexpr int kThreads = 256;
+constexpr int kBatch = 4;                 // pixels per thread per batch
+constexpr uint32_t kPending = 0xFFFFFFFEu;  // in-target pixel without an assignment yet
+constexpr int kEagerMinLevel = 3;         // levels >= this get their cells in phase 0
 
 enum Mode { kAssign = 0, kStylize = 1 };
 
@@ -61,19 +67,23 @@ struct FrameArgs {
     float4 *f32_out;             // sb_blend float variant
 };
 
+// upper bound of the cells of level l touching a region of RW x RH pixels
+__host__ __device__ inline int cells_bound(int RW, int RH, int l) {
+    return (((RW - 1) >> l) + 4) * (((RH - 1) >> l) + 4);
+}
+
 struct SmemLayout {
     int RW, RH, NR, NC;
     size_t off_cells, off_gt, off_A, off_list0, off_list1, off_bytes, off_cnt, total;
 };
 
-__host__ __device__ inline int max_cells_x(int RW) { return (RW - 1) / 2 + 4; }
-
-__host__ __device__ inline SmemLayout smem_layout(int r, bool need_cells) {
+__host__ __device__ inline SmemLayout smem_layout(int r, int levels) {
     SmemLayout s;
     s.RW = kTW + 2 * r;
     s.RH = kTH + 2 * r;
     s.NR = s.RW * s.RH;
-    s.NC = need_cells ? max_cells_x(s.RW) * max_cells_x(s.RH) : 0;
+    s.NC = 0;
+    for (int l = 1; l <= levels; ++l) s.NC += cells_bound(s.RW, s.RH, l);
     size_t o = 0;
     s.off_cells = o;
     o += sizeof(int4) * (size_t)s.NC;
@@ -106,6 +116,56 @@ __device__ __forceinline__ void list_push(bool pred, int val, uint16_t *list, in
     if (pred) list[base + __popc(mask & ((1u << lane) - 1u))] = (uint16_t)val;
 }
 
+// Geometry of the seed cells of level l for the clamped region [xa, xb] x [ya, yb].
+struct LevelCells {
+    int cx0, cy0, ncx, ncy;
+};
+
+__device__ __forceinline__ LevelCells level_cells(int l, int xa, int xb, int ya, int yb) {
+    LevelCells g;
+    g.cx0 = (xa >> l) - 1;
+    g.ncx = (xb >> l) - (xa >> l) + 3;
+    g.cy0 = (ya >> l) - 1;
+    g.ncy = (yb >> l) - (ya >> l) + 3;
+    return g;
+}
+
+// Builds the cells of levels l_hi down to l_lo into cells[base_hi...]; the
+// levels are stacked from l_hi downwards.
+template <int C, int B>
+__device__ __forceinline__ void build_cells(const FrameArgs &a, int4 *cells, int l_hi, int l_lo,
+                                            int base_hi, int xa, int xb, int ya, int yb,
+                                            int cxo, int cyo) {
+    using F = GuideFmt<C, B>;
+    int total = 0;
+    for (int l = l_hi; l >= l_lo; --l) {
+        const LevelCells g = level_cells(l, xa, xb, ya, yb);
+        total += g.ncx * g.ncy;
+    }
+#pragma unroll 2
+    for (int k = threadIdx.x; k < total; k += kThreads) {
+        // locate the level of flat index k (few levels, short scan)
+        int l = l_hi, off = 0;
+        LevelCells g = level_cells(l, xa, xb, ya, yb);
+        while (k >= off + g.ncx * g.ncy) {
+            off += g.ncx * g.ncy;
+            --l;
+            g = level_cells(l, xa, xb, ya, yb);
+        }
+        const int ci = k - off;
+        const int h = 1 << l;
+        const int bx = g.cx0 + ci % g.ncx, by = g.cy0 + ci / g.ncx;
+        const uint32_t hsh = cell_hash(level_key(a.seed, l), bx, by);
+        const int ox = (int)(((hsh & 0xFFFFu) * (uint32_t)h) >> 16);
+        const int oy = (int)(((hsh >> 16) * (uint32_t)h) >> 16);
+        const int sx = min(max(bx * h + ox, 0), a.W - 1);
+        const int sy = min(max(by * h + oy, 0), a.H - 1);
+        const uint32_t u = __ldg(a.lut + F::key(F::load(a.tgt, a.tgt_stride, sx, sy), a.key_bits));
+        const int qx = sx - cxo, qy = sy - cyo;
+        cells[base_hi + k] = make_int4(-2 * qx, -2 * qy, qx * qx + qy * qy, (int)u);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // assignment of the region held in shared memory (Algorithm 2)
 // ---------------------------------------------------------------------------
@@ -121,102 +181,124 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     int *cnt = reinterpret_cast<int *>(smem + L.off_cnt);
     const int tid = threadIdx.x;
 
-    if (tid == 0) cnt[0] = 0;
-    __syncthreads();
-    // phase 0: target guide of the region; in-target pixels start pending
-    for (int i0 = 0; i0 < L.NR; i0 += kThreads) {
-        const int i = i0 + tid;
-        bool inside = false;
-        if (i < L.NR) {
-            const int gx = rx0 + i % L.RW, gy = ry0 + i / L.RW;
-            inside = gx >= 0 && gy >= 0 && gx < a.W && gy < a.H;
-            gt[i] = inside ? F::load(a.tgt, a.tgt_stride, gx, gy) : 0u;
-            A[i] = kInvalid;
-        }
-        list_push(inside, i, list0, &cnt[0]);
-    }
-    __syncthreads();
-    int n_pend = cnt[0];
-
-    // clamped region extent (all pending pixels lie inside it)
+    // clamped region extent (every in-target region pixel lies inside it)
     const int xa = max(rx0, 0), xb = min(rx0 + L.RW, a.W) - 1;
     const int ya = max(ry0, 0), yb = min(ry0 + L.RH, a.H) - 1;
     const int cxo = rx0 + L.RW / 2, cyo = ry0 + L.RH / 2;
     const uint32_t t32 = a.threshold > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)a.threshold;
+    const int L_top = a.levels;
+    const int eager_lo = L_top <= kEagerMinLevel ? 1 : kEagerMinLevel;
+
+    // phase 0: target guide of the region, cells of the coarse levels
+    if (tid == 0) {
+        cnt[0] = 0;
+        cnt[1] = 0;
+    }
+#pragma unroll 4
+    for (int i = tid; i < L.NR; i += kThreads) {
+        const int gx = rx0 + i % L.RW, gy = ry0 + i / L.RW;
+        const bool inside = gx >= 0 && gy >= 0 && gx < a.W && gy < a.H;
+        gt[i] = inside ? F::load(a.tgt, a.tgt_stride, gx, gy) : 0u;
+        A[i] = inside ? kPending : kInvalid;
+    }
+    build_cells<C, B>(a, cells, L_top, eager_lo, 0, xa, xb, ya, yb, cxo, cyo);
+    __syncthreads();
 
     int cur = 0;
-    for (int l = a.levels; l >= 1 && n_pend > 0; --l) {
-        const int h = 1 << l;
-        const int cx0 = (xa >> l) - 1, ncx = (xb >> l) - (xa >> l) + 3;
-        const int cy0 = (ya >> l) - 1, ncy = (yb >> l) - (ya >> l) + 3;
-        const uint32_t lk = level_key(a.seed, l);
-        for (int ci = tid; ci < ncx * ncy; ci += kThreads) {
-            const int bx = cx0 + ci % ncx, by = cy0 + ci / ncx;
-            const uint32_t hsh = cell_hash(lk, bx, by);
-            const int ox = (int)(((hsh & 0xFFFFu) * (uint32_t)h) >> 16);
-            const int oy = (int)(((hsh >> 16) * (uint32_t)h) >> 16);
-            const int sx = min(max(bx * h + ox, 0), a.W - 1);
-            const int sy = min(max(by * h + oy, 0), a.H - 1);
-            const uint32_t u =
-                __ldg(a.lut + F::key(F::load(a.tgt, a.tgt_stride, sx, sy), a.key_bits));
-            const int qx = sx - cxo, qy = sy - cyo;
-            cells[ci] = make_int4(-2 * qx, -2 * qy, qx * qx + qy * qy, (int)u);
+    int n_pend = L.NR;  // the top level scans the whole region
+    int base = 0;       // first cell of the current level
+    for (int l = L_top; l >= 1 && n_pend > 0; --l) {
+        const LevelCells g = level_cells(l, xa, xb, ya, yb);
+        if (l == kEagerMinLevel - 1 && eager_lo > 1) {
+            // a pixel still needs the fine levels: build levels 2 and 1 now
+            build_cells<C, B>(a, cells, l, 1, base, xa, xb, ya, yb, cxo, cyo);
+            __syncthreads();
         }
         const int nxt = cur ^ 1;
         const uint16_t *list_cur = cur ? list1 : list0;
         uint16_t *list_nxt = cur ? list0 : list1;
-        if (tid == 0) cnt[nxt] = 0;
-        __syncthreads();
-        for (int j0 = 0; j0 < n_pend; j0 += kThreads) {
-            const int j = j0 + tid;
-            bool reject = false;
-            int i = 0;
-            if (j < n_pend) {
-                i = list_cur[j];
-                const int rx = i % L.RW, ry = i / L.RW;
-                const int gx = rx0 + rx, gy = ry0 + ry;
-                const int prx = rx - L.RW / 2, pry = ry - L.RH / 2;
-                const int lcx = (gx >> l) - cx0, lcy = (gy >> l) - cy0;
-                int best_e = INT_MAX, best_c = 0;
+        const bool top = l == L_top;
+        for (int j0 = 0; j0 < n_pend; j0 += kThreads * kBatch) {
+            int idx[kBatch];
+            int sxv[kBatch], syv[kBatch];
+            uint32_t gsv[kBatch];
+            bool act[kBatch], inb[kBatch];
 #pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
+            for (int u = 0; u < kBatch; ++u) {
+                const int j = j0 + u * kThreads + tid;
+                act[u] = j < n_pend;
+                int i = 0;
+                if (act[u]) {
+                    i = top ? j : list_cur[j];
+                    if (top) act[u] = A[i] == kPending;
+                }
+                idx[u] = i;
+                inb[u] = false;
+                gsv[u] = 0;
+                sxv[u] = 0;
+                syv[u] = 0;
+                if (act[u]) {
+                    const int rx = i % L.RW, ry = i / L.RW;
+                    const int gx = rx0 + rx, gy = ry0 + ry;
+                    const int prx = rx - L.RW / 2, pry = ry - L.RH / 2;
+                    const int lcx = (gx >> l) - g.cx0, lcy = (gy >> l) - g.cy0;
+                    int best_e = INT_MAX, best_c = 0;
 #pragma unroll
-                    for (int dy = -1; dy <= 1; ++dy) {
-                        const int c = (lcy + dy) * ncx + (lcx + dx);
-                        const int4 cl = cells[c];
-                        const int e = cl.z + cl.x * prx + cl.y * pry;
-                        if (e < best_e) {
-                            best_e = e;
-                            best_c = c;
+                    for (int dx = -1; dx <= 1; ++dx) {
+#pragma unroll
+                        for (int dy = -1; dy <= 1; ++dy) {
+                            const int c = base + (lcy + dy) * g.ncx + (lcx + dx);
+                            const int4 cl = cells[c];
+                            const int e = cl.z + cl.x * prx + cl.y * pry;
+                            if (e < best_e) {
+                                best_e = e;
+                                best_c = c;
+                            }
                         }
                     }
-                }
-                const int4 cl = cells[best_c];
-                int sx = (int)((uint32_t)cl.w & 0xFFFFu) + prx + (cl.x >> 1);
-                int sy = (int)((uint32_t)cl.w >> 16) + pry + (cl.y >> 1);
-                bool acc;
-                if (l > 1) {
-                    acc = (unsigned)sx < (unsigned)a.Ws && (unsigned)sy < (unsigned)a.Hs;
-                    if (acc) {
-                        const uint64_t d = F::dist(F::load(a.src, a.src_stride, sx, sy), gt[i]);
-                        if constexpr (B == 8) acc = (uint32_t)d <= t32;
-                        else acc = d <= a.threshold;
+                    const int4 cl = cells[best_c];
+                    int sx = (int)((uint32_t)cl.w & 0xFFFFu) + prx + (cl.x >> 1);
+                    int sy = (int)((uint32_t)cl.w >> 16) + pry + (cl.y >> 1);
+                    if (l > 1) {
+                        inb[u] = (unsigned)sx < (unsigned)a.Ws && (unsigned)sy < (unsigned)a.Hs;
+                        if (inb[u]) gsv[u] = F::load(a.src, a.src_stride, sx, sy);
+                    } else {
+                        sx = min(max(sx, 0), a.Ws - 1);
+                        sy = min(max(sy, 0), a.Hs - 1);
                     }
-                } else {
-                    sx = min(max(sx, 0), a.Ws - 1);
-                    sy = min(max(sy, 0), a.Hs - 1);
-                    acc = true;
+                    sxv[u] = sx;
+                    syv[u] = sy;
                 }
-                if (acc) {
-                    A[i] = (uint32_t)sx | ((uint32_t)sy << 16);
-                    if (lev) lev[i] = (uint8_t)l;
-                }
-                reject = !acc;
             }
-            list_push(reject, i, list_nxt, &cnt[nxt]);
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                bool acc = false;
+                if (act[u]) {
+                    if (l > 1) {
+                        if (inb[u]) {
+                            const uint64_t d = F::dist(gsv[u], gt[idx[u]]);
+                            if constexpr (B == 8) acc = (uint32_t)d <= t32;
+                            else acc = d <= a.threshold;
+                        }
+                    } else {
+                        acc = true;
+                    }
+                    if (acc) {
+                        A[idx[u]] = (uint32_t)sxv[u] | ((uint32_t)syv[u] << 16);
+                        if (lev) lev[idx[u]] = (uint8_t)l;
+                    }
+                }
+                list_push(act[u] && !acc, idx[u], list_nxt, &cnt[nxt]);
+            }
         }
         __syncthreads();
         n_pend = cnt[nxt];
+        // cnt[cur] was last read before the barrier above; it becomes the next
+        // level's output counter, and the barrier below publishes the reset
+        // before any thread appends to it
+        if (tid == 0) cnt[cur] = 0;
+        base += g.ncx * g.ncy;
+        __syncthreads();
         cur = nxt;
     }
 }
@@ -224,6 +306,88 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
 // ---------------------------------------------------------------------------
 // voting over the tile (Section 3.2)
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 rgba_f32(uint32_t col) {
+    return make_float4(__fdiv_rn((float)(col & 0xFF), 255.f),
+                       __fdiv_rn((float)((col >> 8) & 0xFF), 255.f),
+                       __fdiv_rn((float)((col >> 16) & 0xFF), 255.f),
+                       __fdiv_rn((float)(col >> 24), 255.f));
+}
+
+template <bool F32>
+__device__ __forceinline__ void vote_store(const FrameArgs &a, uint32_t s0, uint32_t s1,
+                                           uint32_t s2, uint32_t s3, uint32_t n, int gx, int gy,
+                                           int k, uint32_t *out_tile) {
+    if constexpr (F32) {
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n) {
+            const float dn = (float)(255u * n);
+            o = make_float4(__fdiv_rn((float)s0, dn), __fdiv_rn((float)s1, dn),
+                            __fdiv_rn((float)s2, dn), __fdiv_rn((float)s3, dn));
+        }
+        a.f32_out[(int64_t)gy * a.W + gx] = o;
+    } else {
+        uint32_t o = 0;
+        if (n) {
+            const uint32_t hn = n >> 1;
+            o = ((s0 + hn) / n) | (((s1 + hn) / n) << 8) | (((s2 + hn) / n) << 16) |
+                (((s3 + hn) / n) << 24);
+        }
+        out_tile[k] = o;
+    }
+}
+
+// Full-window vote of the listed pixels; R > 0 is the radius known at compile
+// time (loads unrolled), R < 0 means the runtime radius a.radius.
+template <int R, bool F32>
+__device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const SmemLayout &L,
+                                               const uint32_t *A, const uint16_t *slow,
+                                               int n_slow, int x0, int y0, uint32_t *out_tile) {
+    const uint32_t *style32 = reinterpret_cast<const uint32_t *>(a.style);
+    const int64_t sstride = a.style_stride >> 2;
+    const int r = R >= 0 ? R : a.radius;
+    for (int j = threadIdx.x; j < n_slow; j += kThreads) {
+        const int k = slow[j];
+        const int tx = k % kTW, ty = k / kTW;
+        const int i = (ty + r) * L.RW + tx + r;
+        uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, n = 0;
+        if constexpr (R >= 0) {
+#pragma unroll
+            for (int oy = -R; oy <= R; ++oy) {
+#pragma unroll
+                for (int ox = -R; ox <= R; ++ox) {
+                    const uint32_t c = A[i + oy * L.RW + ox];
+                    const int vx = (int)(c & 0xFFFFu) - ox, vy = (int)(c >> 16) - oy;
+                    const bool ok = c != kInvalid && (unsigned)vx < (unsigned)a.Ws &&
+                                    (unsigned)vy < (unsigned)a.Hs;
+                    const uint32_t col = ok ? __ldg(style32 + (int64_t)vy * sstride + vx) : 0u;
+                    s0 += col & 0xFFu;
+                    s1 += (col >> 8) & 0xFFu;
+                    s2 += (col >> 16) & 0xFFu;
+                    s3 += col >> 24;
+                    n += ok ? 1u : 0u;
+                }
+            }
+        } else {
+            for (int oy = -r; oy <= r; ++oy) {
+                for (int ox = -r; ox <= r; ++ox) {
+                    const uint32_t c = A[i + oy * L.RW + ox];
+                    if (c == kInvalid) continue;
+                    const int vx = (int)(c & 0xFFFFu) - ox, vy = (int)(c >> 16) - oy;
+                    if ((unsigned)vx >= (unsigned)a.Ws || (unsigned)vy >= (unsigned)a.Hs)
+                        continue;
+                    const uint32_t col = __ldg(style32 + (int64_t)vy * sstride + vx);
+                    s0 += col & 0xFFu;
+                    s1 += (col >> 8) & 0xFFu;
+                    s2 += (col >> 16) & 0xFFu;
+                    s3 += col >> 24;
+                    n += 1;
+                }
+            }
+        }
+        vote_store<F32>(a, s0, s1, s2, s3, n, x0 + tx, y0 + ty, k, out_tile);
+    }
+}
+
 template <bool F32>
 __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &L, int x0,
                                           int y0, const uint32_t *A, uint8_t *hu,
@@ -244,81 +408,52 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
     }
     if (tid == 0) *slow_cnt = 0;
     __syncthreads();
-    // columns: uniform window -> the vote equals the copy C_S[A(p)]
-    for (int k0 = 0; k0 < kTW * kTH; k0 += kThreads) {
-        const int k = k0 + tid;
-        const int tx = k % kTW, ty = k / kTW;
-        const int gx = x0 + tx, gy = y0 + ty;
-        bool need_slow = false;
-        if (gx < a.W && gy < a.H) {
-            const int i = (ty + r) * L.RW + tx + r;
-            const uint32_t c = A[i];
-            const int cx = (int)(c & 0xFFFFu), cy = (int)(c >> 16);
-            bool uni = cx < a.Ws && cy < a.Hs;
-            for (int o = -r; o <= r && uni; ++o)
-                uni = hu[(ty + r + o) * kTW + tx] && A[i + o * L.RW] == c + ((uint32_t)o << 16);
-            if (uni) {
-                const uint32_t col = __ldg(style32 + (int64_t)cy * sstride + cx);
-                if constexpr (F32) {
-                    a.f32_out[(int64_t)gy * a.W + gx] =
-                        make_float4(__fdiv_rn((float)(col & 0xFF), 255.f),
-                                    __fdiv_rn((float)((col >> 8) & 0xFF), 255.f),
-                                    __fdiv_rn((float)((col >> 16) & 0xFF), 255.f),
-                                    __fdiv_rn((float)(col >> 24), 255.f));
-                } else {
-                    out_tile[k] = col;
-                }
-            } else {
-                need_slow = true;
+    // columns: a uniform window votes the copy C_S[A(p)]
+    for (int k0 = 0; k0 < kTW * kTH; k0 += kThreads * kBatch) {
+        uint32_t col[kBatch];
+        bool uni[kBatch], need[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int k = k0 + u * kThreads + tid;
+            const int tx = k % kTW, ty = k / kTW;
+            const int gx = x0 + tx, gy = y0 + ty;
+            uni[u] = false;
+            need[u] = false;
+            col[u] = 0;
+            if (k < kTW * kTH && gx < a.W && gy < a.H) {
+                const int i = (ty + r) * L.RW + tx + r;
+                const uint32_t c = A[i];
+                const int cx = (int)(c & 0xFFFFu), cy = (int)(c >> 16);
+                bool ok = cx < a.Ws && cy < a.Hs;
+                for (int o = -r; o <= r && ok; ++o)
+                    ok = hu[(ty + r + o) * kTW + tx] && A[i + o * L.RW] == c + ((uint32_t)o << 16);
+                uni[u] = ok;
+                need[u] = !ok;
+                if (ok) col[u] = __ldg(style32 + (int64_t)cy * sstride + cx);
             }
         }
-        list_push(need_slow, k, slow, slow_cnt);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int k = k0 + u * kThreads + tid;
+            if (uni[u]) {
+                if constexpr (F32) {
+                    const int gx = x0 + k % kTW, gy = y0 + k / kTW;
+                    a.f32_out[(int64_t)gy * a.W + gx] = rgba_f32(col[u]);
+                } else {
+                    out_tile[k] = col[u];
+                }
+            }
+            list_push(need[u], k, slow, slow_cnt);
+        }
     }
     __syncthreads();
-    // full window for the listed pixels
     const int n_slow = *slow_cnt;
-    for (int j = tid; j < n_slow; j += kThreads) {
-        const int k = slow[j];
-        const int tx = k % kTW, ty = k / kTW;
-        const int i = (ty + r) * L.RW + tx + r;
-        uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, n = 0;
-        uint32_t last_v = kInvalid, last_c = 0;
-        for (int oy = -r; oy <= r; ++oy) {
-            for (int ox = -r; ox <= r; ++ox) {
-                const uint32_t c = A[i + oy * L.RW + ox];
-                if (c == kInvalid) continue;
-                const int vx = (int)(c & 0xFFFFu) - ox, vy = (int)(c >> 16) - oy;
-                if ((unsigned)vx >= (unsigned)a.Ws || (unsigned)vy >= (unsigned)a.Hs) continue;
-                const uint32_t v = (uint32_t)vx | ((uint32_t)vy << 16);
-                if (v != last_v) {
-                    last_c = __ldg(style32 + (int64_t)vy * sstride + vx);
-                    last_v = v;
-                }
-                s0 += last_c & 0xFFu;
-                s1 += (last_c >> 8) & 0xFFu;
-                s2 += (last_c >> 16) & 0xFFu;
-                s3 += last_c >> 24;
-                n += 1;
-            }
-        }
-        const int gx = x0 + tx, gy = y0 + ty;
-        if constexpr (F32) {
-            float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (n) {
-                const float dn = (float)(255u * n);
-                o = make_float4(__fdiv_rn((float)s0, dn), __fdiv_rn((float)s1, dn),
-                                __fdiv_rn((float)s2, dn), __fdiv_rn((float)s3, dn));
-            }
-            a.f32_out[(int64_t)gy * a.W + gx] = o;
-        } else {
-            uint32_t o = 0;
-            if (n) {
-                const uint32_t hn = n >> 1;
-                o = ((s0 + hn) / n) | (((s1 + hn) / n) << 8) | (((s2 + hn) / n) << 16) |
-                    (((s3 + hn) / n) << 24);
-            }
-            out_tile[k] = o;
-        }
+    switch (r) {
+        case 0: vote_slow_list<0, F32>(a, L, A, slow, n_slow, x0, y0, out_tile); break;
+        case 1: vote_slow_list<1, F32>(a, L, A, slow, n_slow, x0, y0, out_tile); break;
+        case 2: vote_slow_list<2, F32>(a, L, A, slow, n_slow, x0, y0, out_tile); break;
+        case 3: vote_slow_list<3, F32>(a, L, A, slow, n_slow, x0, y0, out_tile); break;
+        default: vote_slow_list<-1, F32>(a, L, A, slow, n_slow, x0, y0, out_tile); break;
     }
 }
 
@@ -326,7 +461,7 @@ template <int C, int B, int MODE>
 __global__ void __launch_bounds__(kThreads) frame_kernel(const FrameArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int r = MODE == kStylize ? a.radius : 0;
-    const SmemLayout L = smem_layout(r, true);
+    const SmemLayout L = smem_layout(r, a.levels);
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
     const int rx0 = x0 - r, ry0 = y0 - r;
     uint8_t *bytes = smem + L.off_bytes;
@@ -357,10 +492,11 @@ __global__ void __launch_bounds__(kThreads) frame_kernel(const FrameArgs a) {
 template <bool F32>
 __global__ void __launch_bounds__(kThreads) blend_kernel(const FrameArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout L = smem_layout(a.radius, false);
+    const SmemLayout L = smem_layout(a.radius, 0);
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
     const int rx0 = x0 - a.radius, ry0 = y0 - a.radius;
     uint32_t *A = reinterpret_cast<uint32_t *>(smem + L.off_A);
+#pragma unroll 4
     for (int i = threadIdx.x; i < L.NR; i += kThreads) {
         const int gx = rx0 + i % L.RW, gy = ry0 + i / L.RW;
         const bool inside = gx >= 0 && gy >= 0 && gx < a.W && gy < a.H;
@@ -380,17 +516,18 @@ __global__ void __launch_bounds__(kThreads) blend_kernel(const FrameArgs a) {
     }
 }
 
-// Raises a kernel's dynamic shared-memory limit once per (kernel, device,
-// size class); later launches skip the driver call.
-template <typename K>
-static cudaError_t ensure_smem(K kernel, size_t smem) {
+// Raises a kernel's dynamic shared-memory limit once per (kernel, device);
+// later launches of no larger size skip the driver call.  The cache is keyed
+// by the kernel itself (one static per template instance).
+template <auto Kernel>
+static cudaError_t ensure_smem(size_t smem) {
     constexpr int kMaxDev = 64;
     static std::atomic<uint32_t> done[kMaxDev] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     const uint32_t need = (uint32_t)smem;
     if (dev < kMaxDev && done[dev].load(std::memory_order_relaxed) >= need) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess && dev < kMaxDev) {
         uint32_t cur = done[dev].load();
@@ -400,13 +537,12 @@ static cudaError_t ensure_smem(K kernel, size_t smem) {
     return e;
 }
 
-template <typename K>
-static cudaError_t launch_tiles(K kernel, size_t smem, int W, int H, cudaStream_t s,
-                                const FrameArgs &a) {
-    cudaError_t e = ensure_smem(kernel, smem);
+template <auto Kernel>
+static cudaError_t launch_tiles(size_t smem, int W, int H, cudaStream_t s, const FrameArgs &a) {
+    cudaError_t e = ensure_smem<Kernel>(smem);
     if (e != cudaSuccess) return e;
     dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
-    kernel<<<grid, kThreads, smem, s>>>(a);
+    Kernel<<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -417,8 +553,8 @@ struct FrameLaunch {
     cudaError_t err = cudaSuccess;
     template <int C, int B>
     void operator()() {
-        const SmemLayout L = smem_layout(MODE == kStylize ? a->radius : 0, true);
-        err = launch_tiles(frame_kernel<C, B, MODE>, L.total, a->W, a->H, s, *a);
+        const SmemLayout L = smem_layout(MODE == kStylize ? a->radius : 0, a->levels);
+        err = launch_tiles<frame_kernel<C, B, MODE>>(L.total, a->W, a->H, s, *a);
     }
 };
 
@@ -541,10 +677,10 @@ extern "C" sb_status sb_blend(const uint32_t *assign, int32_t tgt_w, int32_t tgt
     a.assign_in = assign;
     a.rgba_out = reinterpret_cast<uint32_t *>(rgba8_out);
     a.f32_out = reinterpret_cast<float4 *>(rgba32f_out);
-    const SmemLayout L = smem_layout(blend_radius, false);
+    const SmemLayout L = smem_layout(blend_radius, 0);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    e = rgba32f_out ? launch_tiles(blend_kernel<true>, L.total, tgt_w, tgt_h, s, a)
-                    : launch_tiles(blend_kernel<false>, L.total, tgt_w, tgt_h, s, a);
+    e = rgba32f_out ? launch_tiles<blend_kernel<true>>(L.total, tgt_w, tgt_h, s, a)
+                    : launch_tiles<blend_kernel<false>>(L.total, tgt_w, tgt_h, s, a);
     if (e != cudaSuccess) return cuda_fail(e, "sb_blend");
     return ok();
 }
