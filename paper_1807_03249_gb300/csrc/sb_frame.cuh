@@ -1,0 +1,745 @@
+// Per-frame StyleBlit kernels: Algorithm 2 (ParallelStyleBlit) with the
+// coordinate transfer and voting step of Section 3.2.  Templates only; the
+// sb_frame_*.cu files instantiate them per guide format.
+//
+// One CTA owns a 64 x 32 output tile.  The fused kernel computes the
+// assignment A of the tile plus a halo of R pixels (the vote window) in shared
+// memory, so A never reaches device memory:
+//
+//   phase 0  target guide of the region -> smem (one packed uint32 per pixel);
+//            the seed cells of every level >= 3 are built at the same time
+//            (levels 2 and 1 have many cells and are built only if a pixel of
+//            the tile still needs them).  A cell is: jitter hash -> seed q
+//            clamped into the target -> G_T[q] -> table entry u*(q).  Cells are
+//            stored column-major (x outer, y inner), each as (-2q, |q|^2, u*)
+//            in region-centred coordinates, pre-scaled by 2^11 with the cell's
+//            column-major index in the low 11 bits.
+//   levels   for l = L..1 while pixels are pending, each pending pixel p takes
+//            the minimum over its 3 x 3 cells of |q|^2 - 2 q.p (which orders
+//            seeds like |q - p|^2) packed with the cell index: one min gives
+//            the nearest seed and, on ties, the first cell in x-outer,
+//            y-inner order, as NearestSeed's strict < does.  The candidate
+//            s = u* + (p - q) is accepted if it lies in the source and
+//            |G_S[s] - G_T[p]|^2 <= t (level 1 always accepts, s clamped).
+//            Pixels go four per thread per batch with their gathers issued
+//            first; rejected ones are compacted into the next pending list.
+//   vote     ballot bitmasks mark, per row, where A steps by exactly one pixel
+//            (horizontally and vertically); a window made of one translation
+//            votes exactly C_S[A(p)], a plain copy.  Other pixels (chunk
+//            boundaries, frame borders) are compacted and summed over the full
+//            window with integer sums and round-half-up division.
+//   store    the tile leaves shared memory with coalesced 32-bit stores.
+#pragma once
+
+#include <atomic>
+#include <climits>
+
+#include "sb_internal.cuh"
+
+namespace sb {
+
+constexpr int kTW = 64;
+constexpr int kTH = 32;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kBatch = 4;                   // pixels per thread per batch
+constexpr uint32_t kPending = 0xFFFFFFFEu;  // in-target pixel without an assignment yet
+constexpr int kEagerMinLevel = 3;           // levels >= this get their cells in phase 0
+constexpr int kKeyShift = 11;               // cell-index bits of the packed seed key
+constexpr int kPackedMaxLevel = 8;          // levels whose packed keys fit 32 bits
+
+enum Mode { kAssign = 0, kStylize = 1 };
+
+struct FrameArgs {
+    const uint8_t *tgt;
+    int64_t tgt_stride;
+    int W, H;
+    const uint32_t *src_packed;  // G_S, one packed uint32 per pixel, row-major
+    int Ws, Hs;
+    const uint32_t *lut;
+    int key_bits;
+    const uint8_t *style;
+    int64_t style_stride;
+    int levels;
+    uint64_t threshold;
+    uint32_t seed;
+    int radius;
+    const uint32_t *assign_in;   // sb_blend
+    uint32_t *assign_out;        // sb_assign_chunks
+    uint8_t *level_out;          // sb_assign_chunks (nullable)
+    uint32_t *rgba_out;          // RGBA8 as one uint32 per pixel
+    float4 *f32_out;             // sb_blend float variant
+};
+
+// upper bound of the cells of level l touching a region of RW x RH pixels
+__host__ __device__ constexpr int cells_bound(int RW, int RH, int l) {
+    return (((RW - 1) >> l) + 4) * (((RH - 1) >> l) + 4);
+}
+
+struct SmemLayout {
+    int RW, RH, NR, NC;
+    size_t off_cells, off_gt, off_A, off_list0, off_list1, off_bytes, off_masks, off_cnt, total;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int r, int levels) {
+    SmemLayout s;
+    s.RW = kTW + 2 * r;
+    s.RH = kTH + 2 * r;
+    s.NR = s.RW * s.RH;
+    s.NC = 0;
+    for (int l = 1; l <= levels; ++l) s.NC += cells_bound(s.RW, s.RH, l);
+    size_t o = 0;
+    s.off_cells = o;
+    o += sizeof(int4) * (size_t)s.NC;
+    s.off_gt = o;
+    o += sizeof(uint32_t) * (size_t)s.NR;
+    s.off_A = o;
+    o += sizeof(uint32_t) * (size_t)s.NR;
+    s.off_masks = o;
+    o += (2 * sizeof(uint64_t) + 4 * sizeof(uint32_t)) * (size_t)s.RH;
+    s.off_list0 = o;
+    o += sizeof(uint16_t) * (size_t)s.NR;
+    s.off_list1 = o;
+    o += sizeof(uint16_t) * (size_t)s.NR;
+    s.off_bytes = o;
+    o += (size_t)s.NR;
+    o = (o + 15) & ~(size_t)15;
+    s.off_cnt = o;
+    o += 16;
+    s.total = o;
+    return s;
+}
+
+// Block-wide append to a shared list; every lane of the warp must call it.
+__device__ __forceinline__ void list_push(bool pred, int val, uint16_t *list, int *counter) {
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
+    if (mask == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(mask));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (pred) list[base + __popc(mask & ((1u << lane) - 1u))] = (uint16_t)val;
+}
+
+// Seed cells of level l for the clamped region [xa, xb] x [ya, yb].
+struct LevelCells {
+    int cx0, cy0, ncx, ncy;
+};
+
+__device__ __forceinline__ LevelCells level_cells(int l, int xa, int xb, int ya, int yb) {
+    LevelCells g;
+    g.cx0 = (xa >> l) - 1;
+    g.ncx = (xb >> l) - (xa >> l) + 3;
+    g.cy0 = (ya >> l) - 1;
+    g.ncy = (yb >> l) - (ya >> l) + 3;
+    return g;
+}
+
+// Builds the cells of levels l_hi down to l_lo into cells[base_hi...]; the
+// levels are stacked from l_hi downwards, each column-major.
+template <int C, int B>
+__device__ __forceinline__ void build_cells(const FrameArgs &a, int4 *cells, int l_hi, int l_lo,
+                                            int base_hi, int xa, int xb, int ya, int yb,
+                                            int cxo, int cyo) {
+    using F = GuideFmt<C, B>;
+    int total = 0;
+    for (int l = l_hi; l >= l_lo; --l) {
+        const LevelCells g = level_cells(l, xa, xb, ya, yb);
+        total += g.ncx * g.ncy;
+    }
+#pragma unroll 2
+    for (int k = threadIdx.x; k < total; k += kThreads) {
+        int l = l_hi, off = 0;
+        LevelCells g = level_cells(l, xa, xb, ya, yb);
+        while (k >= off + g.ncx * g.ncy) {
+            off += g.ncx * g.ncy;
+            --l;
+            g = level_cells(l, xa, xb, ya, yb);
+        }
+        const int ci = k - off;               // column-major: ci = lcx * ncy + lcy
+        const int lcx = ci / g.ncy, lcy = ci - lcx * g.ncy;
+        const int h = 1 << l;
+        const int bx = g.cx0 + lcx, by = g.cy0 + lcy;
+        const uint32_t hsh = cell_hash(level_key(a.seed, l), bx, by);
+        const int ox = (int)(((hsh & 0xFFFFu) * (uint32_t)h) >> 16);
+        const int oy = (int)(((hsh >> 16) * (uint32_t)h) >> 16);
+        const int sx = min(max(bx * h + ox, 0), a.W - 1);
+        const int sy = min(max(by * h + oy, 0), a.H - 1);
+        const uint32_t u =
+            __ldg(a.lut + F::key(F::load(a.tgt, a.tgt_stride, sx, sy), a.key_bits));
+        const int qx = sx - cxo, qy = sy - cyo;
+        int4 cell;
+        if (l <= kPackedMaxLevel) {
+            constexpr int S = 1 << kKeyShift;
+            cell = make_int4(-2 * qx * S, -2 * qy * S, (qx * qx + qy * qy) * S + ci, (int)u);
+        } else {
+            cell = make_int4(-2 * qx, -2 * qy, qx * qx + qy * qy, (int)u);
+        }
+        cells[base_hi + k] = cell;
+    }
+}
+
+// Nearest seed of region pixel (prx, pry) (region-centred) at level l: returns
+// the chosen cell; qneg = -q in region-centred coordinates.
+__device__ __forceinline__ int4 nearest_cell(const int4 *cells, int base, int c0, int ncy, int l,
+                                             int prx, int pry, int &qneg_x, int &qneg_y) {
+    if (l <= kPackedMaxLevel) {
+        int key = INT_MAX;
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int4 cl = cells[c0 + dx * ncy + dy];
+                key = min(key, cl.z + cl.x * prx + cl.y * pry);
+            }
+        }
+        const int4 cl = cells[base + (key & ((1 << kKeyShift) - 1))];
+        qneg_x = cl.x >> (kKeyShift + 1);
+        qneg_y = cl.y >> (kKeyShift + 1);
+        return cl;
+    }
+    int best_e = INT_MAX, best_c = c0;
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int c = c0 + dx * ncy + dy;
+            const int4 cl = cells[c];
+            const int e = cl.z + cl.x * prx + cl.y * pry;
+            if (e < best_e) {
+                best_e = e;
+                best_c = c;
+            }
+        }
+    }
+    const int4 cl = cells[best_c];
+    qneg_x = cl.x >> 1;
+    qneg_y = cl.y >> 1;
+    return cl;
+}
+
+// ---------------------------------------------------------------------------
+// assignment of the region held in shared memory (Algorithm 2)
+// ---------------------------------------------------------------------------
+template <int C, int B, int R>
+__device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayout &L, int rx0,
+                                              int ry0, unsigned char *smem, uint8_t *lev) {
+    using F = GuideFmt<C, B>;
+    constexpr int RW = kTW + 2 * R, RH = kTH + 2 * R, NR = RW * RH;
+    int4 *cells = reinterpret_cast<int4 *>(smem + L.off_cells);
+    uint32_t *gt = reinterpret_cast<uint32_t *>(smem + L.off_gt);
+    uint32_t *A = reinterpret_cast<uint32_t *>(smem + L.off_A);
+    uint16_t *const list0 = reinterpret_cast<uint16_t *>(smem + L.off_list0);
+    uint16_t *const list1 = reinterpret_cast<uint16_t *>(smem + L.off_list1);
+    int *cnt = reinterpret_cast<int *>(smem + L.off_cnt);
+    const int tid = threadIdx.x;
+
+    const int xa = max(rx0, 0), xb = min(rx0 + RW, a.W) - 1;
+    const int ya = max(ry0, 0), yb = min(ry0 + RH, a.H) - 1;
+    const int cxo = rx0 + RW / 2, cyo = ry0 + RH / 2;
+    const uint32_t t32 = a.threshold > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)a.threshold;
+    const int L_top = a.levels;
+    const int eager_lo = L_top <= kEagerMinLevel ? 1 : kEagerMinLevel;
+
+    if (tid == 0) {
+        cnt[0] = 0;
+        cnt[1] = 0;
+    }
+#pragma unroll 4
+    for (int i = tid; i < NR; i += kThreads) {
+        const int gx = rx0 + i % RW, gy = ry0 + i / RW;
+        const bool inside = gx >= 0 && gy >= 0 && gx < a.W && gy < a.H;
+        gt[i] = inside ? F::load(a.tgt, a.tgt_stride, gx, gy) : 0u;
+        A[i] = inside ? kPending : kInvalid;
+    }
+    build_cells<C, B>(a, cells, L_top, eager_lo, 0, xa, xb, ya, yb, cxo, cyo);
+    __syncthreads();
+
+    int cur = 0;
+    int n_pend = NR;  // the top level scans the whole region
+    int base = 0;     // first cell of the current level
+    for (int l = L_top; l >= 1 && n_pend > 0; --l) {
+        const LevelCells g = level_cells(l, xa, xb, ya, yb);
+        if (l == kEagerMinLevel - 1 && eager_lo > 1) {
+            // a pixel still needs the fine levels: build levels 2 and 1 now
+            build_cells<C, B>(a, cells, l, 1, base, xa, xb, ya, yb, cxo, cyo);
+            __syncthreads();
+        }
+        const int nxt = cur ^ 1;
+        const uint16_t *list_cur = cur ? list1 : list0;
+        uint16_t *list_nxt = cur ? list0 : list1;
+        const bool top = l == L_top;
+        for (int j0 = 0; j0 < n_pend; j0 += kThreads * kBatch) {
+            int idx[kBatch];
+            uint32_t sv[kBatch], gsv[kBatch];
+            bool act[kBatch], inb[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int j = j0 + u * kThreads + tid;
+                act[u] = j < n_pend;
+                int i = 0;
+                if (act[u]) {
+                    i = top ? j : list_cur[j];
+                    if (top) act[u] = A[i] == kPending;
+                }
+                idx[u] = i;
+                inb[u] = false;
+                gsv[u] = 0;
+                sv[u] = 0;
+                if (act[u]) {
+                    const int rx = i % RW, ry = i / RW;
+                    const int prx = rx - RW / 2, pry = ry - RH / 2;
+                    const int lcx = ((rx0 + rx) >> l) - g.cx0, lcy = ((ry0 + ry) >> l) - g.cy0;
+                    int qnx, qny;
+                    const int4 cl = nearest_cell(cells, base, base + lcx * g.ncy + lcy, g.ncy, l,
+                                                 prx, pry, qnx, qny);
+                    int sx = (int)((uint32_t)cl.w & 0xFFFFu) + prx + qnx;
+                    int sy = (int)((uint32_t)cl.w >> 16) + pry + qny;
+                    if (l > 1) {
+                        inb[u] = (unsigned)sx < (unsigned)a.Ws && (unsigned)sy < (unsigned)a.Hs;
+                        if (inb[u]) gsv[u] = __ldg(a.src_packed + (int64_t)sy * a.Ws + sx);
+                    } else {
+                        sx = min(max(sx, 0), a.Ws - 1);
+                        sy = min(max(sy, 0), a.Hs - 1);
+                    }
+                    sv[u] = (uint32_t)sx | ((uint32_t)sy << 16);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                bool acc = false;
+                if (act[u]) {
+                    if (l > 1) {
+                        if (inb[u]) {
+                            const uint64_t d = F::dist(gsv[u], gt[idx[u]]);
+                            if constexpr (B == 8) acc = (uint32_t)d <= t32;
+                            else acc = d <= a.threshold;
+                        }
+                    } else {
+                        acc = true;
+                    }
+                    if (acc) {
+                        A[idx[u]] = sv[u];
+                        if (lev) lev[idx[u]] = (uint8_t)l;
+                    }
+                }
+                list_push(act[u] && !acc, idx[u], list_nxt, &cnt[nxt]);
+            }
+        }
+        __syncthreads();
+        n_pend = cnt[nxt];
+        // cnt[cur] was last read before the barrier above; it becomes the next
+        // level's output counter, and the barrier below publishes the reset
+        // before any thread appends to it
+        if (tid == 0) cnt[cur] = 0;
+        base += g.ncx * g.ncy;
+        __syncthreads();
+        cur = nxt;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// voting over the tile (Section 3.2)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 rgba_f32(uint32_t col) {
+    return make_float4(__fdiv_rn((float)(col & 0xFF), 255.f),
+                       __fdiv_rn((float)((col >> 8) & 0xFF), 255.f),
+                       __fdiv_rn((float)((col >> 16) & 0xFF), 255.f),
+                       __fdiv_rn((float)(col >> 24), 255.f));
+}
+
+// Channel sums of a vote.  Windows of at most 15 x 15 taps keep two channels
+// per 32-bit word (16-bit lanes: 225 * 255 < 2^16); larger ones one per word.
+template <bool kPacked>
+struct VoteAcc;
+
+template <>
+struct VoteAcc<true> {
+    uint32_t lo = 0, hi = 0, n = 0;  // lo = c0 | c2 << 16, hi = c1 | c3 << 16
+    __device__ __forceinline__ void add(uint32_t col, uint32_t cnt) {
+        lo += (col & 0x00FF00FFu) * cnt;
+        hi += ((col >> 8) & 0x00FF00FFu) * cnt;
+        n += cnt;
+    }
+    __device__ __forceinline__ void sums(uint32_t &s0, uint32_t &s1, uint32_t &s2,
+                                         uint32_t &s3) const {
+        s0 = lo & 0xFFFFu;
+        s2 = lo >> 16;
+        s1 = hi & 0xFFFFu;
+        s3 = hi >> 16;
+    }
+};
+
+template <>
+struct VoteAcc<false> {
+    uint32_t s[4] = {0, 0, 0, 0}, n = 0;
+    __device__ __forceinline__ void add(uint32_t col, uint32_t cnt) {
+        s[0] += (col & 0xFFu) * cnt;
+        s[1] += ((col >> 8) & 0xFFu) * cnt;
+        s[2] += ((col >> 16) & 0xFFu) * cnt;
+        s[3] += (col >> 24) * cnt;
+        n += cnt;
+    }
+    __device__ __forceinline__ void sums(uint32_t &s0, uint32_t &s1, uint32_t &s2,
+                                         uint32_t &s3) const {
+        s0 = s[0];
+        s1 = s[1];
+        s2 = s[2];
+        s3 = s[3];
+    }
+};
+
+// Round-half-up quotient (s + n/2) / n for n >= 1 via a multiply-high:
+// floor(y / n) == umulhi(y, floor((2^32 - 1) / n) + 1) for every n in
+// [2, 961] and y <= 255 n + n / 2 (checked exhaustively); n == 1 is y.
+__device__ __forceinline__ uint32_t div_round(uint32_t s, uint32_t n, uint32_t m) {
+    const uint32_t y = s + (n >> 1);
+    return n == 1 ? y : __umulhi(y, m);
+}
+
+template <bool F32, typename Acc>
+__device__ __forceinline__ void vote_store(const FrameArgs &a, const Acc &acc, int gx, int gy,
+                                           int k, uint32_t *out_tile) {
+    uint32_t s0, s1, s2, s3;
+    acc.sums(s0, s1, s2, s3);
+    const uint32_t n = acc.n;
+    if constexpr (F32) {
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n) {
+            const float dn = (float)(255u * n);
+            o = make_float4(__fdiv_rn((float)s0, dn), __fdiv_rn((float)s1, dn),
+                            __fdiv_rn((float)s2, dn), __fdiv_rn((float)s3, dn));
+        }
+        a.f32_out[(int64_t)gy * a.W + gx] = o;
+    } else {
+        uint32_t o = 0;
+        if (n) {
+            const uint32_t m = 0xFFFFFFFFu / n + 1u;
+            o = div_round(s0, n, m) | (div_round(s1, n, m) << 8) | (div_round(s2, n, m) << 16) |
+                (div_round(s3, n, m) << 24);
+        }
+        out_tile[k] = o;
+    }
+}
+
+// Full-window vote of the listed pixels.  Along a window row, taps whose A
+// steps by exactly one pixel form a run sharing one source position
+// v = A(n) - o, so a run contributes len * C_S[v] with a single gather.  A
+// row's run breaks come from the stored step bits E.  Pass 1 sums every
+// listed pixel as if each window row had at most two runs (branch-free: two
+// gathers per row) and compacts the pixels where some row has more breaks
+// (junctions of chunks, frame borders) into a second list; pass 2 sums those
+// tap by tap.  Every lane of a warp runs pass 1's loop the same number of
+// times (the compaction is warp-collective).
+template <int R, bool F32>
+__device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const uint32_t *A,
+                                               const uint32_t *E, const uint16_t *slow,
+                                               int n_slow, uint16_t *cplx, int *cplx_cnt,
+                                               int x0, int y0, uint32_t *out_tile) {
+    constexpr int RW = kTW + 2 * R;
+    constexpr bool kPacked = (2 * R + 1) * (2 * R + 1) * 255 < 65536;
+    constexpr uint32_t kBreakMask = (2 * R >= 32) ? 0xFFFFFFFFu : ((1u << (2 * R)) - 1u);
+    const uint32_t *style32 = reinterpret_cast<const uint32_t *>(a.style);
+    const int64_t sstride = a.style_stride >> 2;
+    auto tap = [&](VoteAcc<kPacked> &acc, const uint32_t *row, int tx, int col, int oy,
+                   uint32_t len) {
+        const uint32_t c = row[col];
+        const uint32_t v = c - (uint32_t)((col - tx - R) + (oy << 16));
+        const uint32_t vx = v & 0xFFFFu, vy = v >> 16;
+        const bool ok = len != 0u && c != kInvalid && vx < (uint32_t)a.Ws && vy < (uint32_t)a.Hs;
+        const uint32_t colr = ok ? __ldg(style32 + (int64_t)vy * sstride + vx) : 0u;
+        acc.add(colr, ok ? len : 0u);
+    };
+    if (threadIdx.x == 0) *cplx_cnt = 0;
+    __syncthreads();
+    for (int j0 = 0; j0 < n_slow; j0 += kThreads) {
+        const int j = j0 + threadIdx.x;
+        const bool act = j < n_slow;
+        const int k = act ? slow[j] : 0;
+        const int tx = k % kTW, ty = k / kTW;
+        bool complex_row = false;
+        if (act) {
+            VoteAcc<kPacked> acc;
+#pragma unroll
+            for (int oy = -R; oy <= R; ++oy) {
+                const int ry = ty + R + oy;
+                const uint32_t *row = A + ry * RW;
+                const uint32_t *e = E + ry * 4;
+                const int b = tx + 1, w = b >> 5;
+                const uint32_t m = ~__funnelshift_r(e[w], e[w + 1], b & 31) & kBreakMask;
+                const int pc = __popc(m);
+                complex_row |= pc > 1;
+                const int j1 = pc ? __ffs(m) - 1 : 2 * R;
+                tap(acc, row, tx, tx, oy, (uint32_t)(j1 + 1));
+                tap(acc, row, tx, min(tx + j1 + 1, tx + 2 * R), oy,
+                    pc == 1 ? (uint32_t)(2 * R - j1) : 0u);
+            }
+            if (!complex_row) vote_store<F32>(a, acc, x0 + tx, y0 + ty, k, out_tile);
+        }
+        list_push(act && complex_row, k, cplx, cplx_cnt);
+    }
+    __syncthreads();
+    const int n_cplx = *cplx_cnt;
+    for (int j = threadIdx.x; j < n_cplx; j += kThreads) {
+        const int k = cplx[j];
+        const int tx = k % kTW, ty = k / kTW;
+        VoteAcc<kPacked> acc;
+        for (int oy = -R; oy <= R; ++oy) {
+            const uint32_t *row = A + (ty + R + oy) * RW;
+#pragma unroll
+            for (int ox = 0; ox <= 2 * R; ++ox) tap(acc, row, tx, tx + ox, oy, 1u);
+        }
+        vote_store<F32>(a, acc, x0 + tx, y0 + ty, k, out_tile);
+    }
+}
+
+// bits [j, j + 64) of the 128-bit value hi:lo
+__device__ __forceinline__ uint64_t shr128(uint64_t lo, uint64_t hi, int j) {
+    return j == 0 ? lo : ((lo >> j) | (hi << (64 - j)));
+}
+
+template <int R, bool F32>
+__device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &L, int x0,
+                                          int y0, const uint32_t *A, unsigned char *smem,
+                                          uint32_t *out_tile) {
+    constexpr int RW = kTW + 2 * R, RH = kTH + 2 * R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t *hu_row = reinterpret_cast<uint64_t *>(smem + L.off_masks);
+    uint64_t *v_row = hu_row + RH;
+    uint32_t *E_row = reinterpret_cast<uint32_t *>(v_row + RH);  // 4 words per region row
+    uint16_t *slow = reinterpret_cast<uint16_t *>(smem + L.off_list0);
+    int *slow_cnt = reinterpret_cast<int *>(smem + L.off_cnt) + 2;
+    const uint32_t *style32 = reinterpret_cast<const uint32_t *>(a.style);
+    const int64_t sstride = a.style_stride >> 2;
+
+    if (threadIdx.x == 0) *slow_cnt = 0;
+    if constexpr (R > 0) {
+        // per region row: E bit x <=> A[x] == A[x-1] + 1 (both valid);
+        // hu bit tx <=> E bits tx+1 .. tx+2R all set (columns tx..tx+2R form
+        // one horizontal translation); v bit tx <=> A[ry][tx+R] == A[ry-1][tx+R]
+        // one row down (both valid)
+        for (int ry = warp; ry < RH; ry += kWarps) {
+            const uint32_t *row = A + ry * RW;
+            uint32_t e[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int x = c * 32 + lane;
+                bool bit = false;
+                if (x >= 1 && x < RW) {
+                    const uint32_t cur = row[x], prv = row[x - 1];
+                    bit = cur != kInvalid && prv != kInvalid && cur == prv + 1u;
+                }
+                e[c] = __ballot_sync(0xFFFFFFFFu, bit);
+            }
+            const uint64_t lo = (uint64_t)e[0] | ((uint64_t)e[1] << 32), hi = e[2];
+            uint64_t hu = ~0ull;
+#pragma unroll
+            for (int j = 1; j <= 2 * R; ++j) hu &= shr128(lo, hi, j);
+            uint32_t v[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int x = c * 32 + lane + R;
+                bool bit = false;
+                if (ry >= 1) {
+                    const uint32_t cur = row[x], up = row[x - RW];
+                    bit = cur != kInvalid && up != kInvalid && cur == up + 0x10000u;
+                }
+                v[c] = __ballot_sync(0xFFFFFFFFu, bit);
+            }
+            if (lane == 0) {
+                hu_row[ry] = hu;
+                v_row[ry] = (uint64_t)v[0] | ((uint64_t)v[1] << 32);
+                E_row[4 * ry + 0] = e[0];
+                E_row[4 * ry + 1] = e[1];
+                E_row[4 * ry + 2] = e[2];
+                E_row[4 * ry + 3] = 0u;
+            }
+        }
+    }
+    __syncthreads();
+    // output rows: warp w takes rows w, w + 8, ...; a uniform window copies
+    constexpr int kRowsPerWarp = kTH / kWarps;
+    uint32_t col[kRowsPerWarp][2];
+    bool uni[kRowsPerWarp][2], need[kRowsPerWarp][2];
+#pragma unroll
+    for (int q = 0; q < kRowsPerWarp; ++q) {
+        const int ty = warp + q * kWarps;
+        uint64_t U = ~0ull;
+        if constexpr (R > 0) {
+#pragma unroll
+            for (int kk = 0; kk <= 2 * R; ++kk) U &= hu_row[ty + kk];
+#pragma unroll
+            for (int kk = 1; kk <= 2 * R; ++kk) U &= v_row[ty + kk];
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int tx = c * 32 + lane;
+            const int gx = x0 + tx, gy = y0 + ty;
+            uni[q][c] = need[q][c] = false;
+            col[q][c] = 0;
+            if (gx < a.W && gy < a.H) {
+                const uint32_t cc = A[(ty + R) * RW + tx + R];
+                const int cx = (int)(cc & 0xFFFFu), cy = (int)(cc >> 16);
+                const bool ok = ((U >> tx) & 1ull) && cx < a.Ws && cy < a.Hs;
+                uni[q][c] = ok;
+                need[q][c] = !ok;
+                if (ok) col[q][c] = __ldg(style32 + (int64_t)cy * sstride + cx);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kRowsPerWarp; ++q) {
+        const int ty = warp + q * kWarps;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int tx = c * 32 + lane;
+            const int k = ty * kTW + tx;
+            if (uni[q][c]) {
+                if constexpr (F32) {
+                    a.f32_out[(int64_t)(y0 + ty) * a.W + x0 + tx] = rgba_f32(col[q][c]);
+                } else {
+                    out_tile[k] = col[q][c];
+                }
+            }
+            list_push(need[q][c], k, slow, slow_cnt);
+        }
+    }
+    __syncthreads();
+    vote_slow_list<R, F32>(a, A, E_row, slow, *slow_cnt,
+                           reinterpret_cast<uint16_t *>(smem + L.off_list1), slow_cnt + 1, x0,
+                           y0, out_tile);
+}
+
+template <int C, int B, int MODE, int R>
+__global__ void __launch_bounds__(kThreads, 3) frame_kernel(const FrameArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmemLayout L = smem_layout(R, a.levels);
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+    uint8_t *bytes = smem + L.off_bytes;
+    assign_region<C, B, R>(a, L, x0 - R, y0 - R, smem, MODE == kAssign ? bytes : nullptr);
+    const uint32_t *A = reinterpret_cast<const uint32_t *>(smem + L.off_A);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (MODE == kAssign) {
+        for (int ty = warp; ty < kTH; ty += kWarps) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int tx = c * 32 + lane;
+                const int gx = x0 + tx, gy = y0 + ty;
+                if (gx < a.W && gy < a.H) {
+                    a.assign_out[(int64_t)gy * a.W + gx] = A[ty * kTW + tx];
+                    if (a.level_out) a.level_out[(int64_t)gy * a.W + gx] = bytes[ty * kTW + tx];
+                }
+            }
+        }
+    } else {
+        // the target guide is no longer needed: its slot holds the output tile
+        uint32_t *out_tile = reinterpret_cast<uint32_t *>(smem + L.off_gt);
+        vote_tile<R, false>(a, L, x0, y0, A, smem, out_tile);
+        __syncthreads();
+        for (int ty = warp; ty < kTH; ty += kWarps) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int tx = c * 32 + lane;
+                const int gx = x0 + tx, gy = y0 + ty;
+                if (gx < a.W && gy < a.H) a.rgba_out[(int64_t)gy * a.W + gx] = out_tile[ty * kTW + tx];
+            }
+        }
+    }
+}
+
+template <bool F32, int R>
+__global__ void __launch_bounds__(kThreads) blend_kernel(const FrameArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int RW = kTW + 2 * R, NR = RW * (kTH + 2 * R);
+    const SmemLayout L = smem_layout(R, 0);
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+    const int rx0 = x0 - R, ry0 = y0 - R;
+    uint32_t *A = reinterpret_cast<uint32_t *>(smem + L.off_A);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < NR; i += kThreads) {
+        const int gx = rx0 + i % RW, gy = ry0 + i / RW;
+        const bool inside = gx >= 0 && gy >= 0 && gx < a.W && gy < a.H;
+        A[i] = inside ? __ldg(a.assign_in + (int64_t)gy * a.W + gx) : kInvalid;
+    }
+    __syncthreads();
+    uint32_t *out_tile = reinterpret_cast<uint32_t *>(smem + L.off_gt);
+    vote_tile<R, F32>(a, L, x0, y0, A, smem, out_tile);
+    if constexpr (!F32) {
+        __syncthreads();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int ty = warp; ty < kTH; ty += kWarps) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int tx = c * 32 + lane;
+                const int gx = x0 + tx, gy = y0 + ty;
+                if (gx < a.W && gy < a.H) a.rgba_out[(int64_t)gy * a.W + gx] = out_tile[ty * kTW + tx];
+            }
+        }
+    }
+}
+
+// Raises a kernel's dynamic shared-memory limit once per (kernel, device);
+// later launches of no larger size skip the driver call.  The cache is keyed
+// by the kernel itself (one static per template instance).
+template <auto Kernel>
+cudaError_t ensure_smem(size_t smem) {
+    constexpr int kMaxDev = 64;
+    static std::atomic<uint32_t> done[kMaxDev] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint32_t need = (uint32_t)smem;
+    if (dev < kMaxDev && done[dev].load(std::memory_order_relaxed) >= need) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess && dev < kMaxDev) {
+        uint32_t cur = done[dev].load();
+        while (cur < need && !done[dev].compare_exchange_weak(cur, need)) {
+        }
+    }
+    return e;
+}
+
+template <auto Kernel>
+cudaError_t launch_tiles(size_t smem, int W, int H, cudaStream_t s, const FrameArgs &a) {
+    cudaError_t e = ensure_smem<Kernel>(smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
+    Kernel<<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int C, int B, int R>
+cudaError_t launch_stylize_r(const FrameArgs &a, cudaStream_t s) {
+    return launch_tiles<frame_kernel<C, B, kStylize, R>>(smem_layout(R, a.levels).total, a.W,
+                                                        a.H, s, a);
+}
+
+// Launches the frame kernel of guide format <C, B> in the given mode.
+template <int C, int B>
+cudaError_t launch_frame(int mode, const FrameArgs &a, cudaStream_t s) {
+    if (mode == kAssign)
+        return launch_tiles<frame_kernel<C, B, kAssign, 0>>(smem_layout(0, a.levels).total, a.W,
+                                                            a.H, s, a);
+    switch (a.radius) {
+        case 0: return launch_stylize_r<C, B, 0>(a, s);
+        case 1: return launch_stylize_r<C, B, 1>(a, s);
+        case 2: return launch_stylize_r<C, B, 2>(a, s);
+        case 3: return launch_stylize_r<C, B, 3>(a, s);
+        case 4: return launch_stylize_r<C, B, 4>(a, s);
+        case 5: return launch_stylize_r<C, B, 5>(a, s);
+        case 6: return launch_stylize_r<C, B, 6>(a, s);
+        case 7: return launch_stylize_r<C, B, 7>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// per-format launchers, one translation unit each (sb_frame_c<C>b<B>.cu)
+cudaError_t launch_frame_c1b8(int mode, const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_frame_c2b8(int mode, const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_frame_c3b8(int mode, const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_frame_c4b8(int mode, const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_frame_c1b16(int mode, const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_frame_c2b16(int mode, const FrameArgs &a, cudaStream_t s);
+
+}  // namespace sb

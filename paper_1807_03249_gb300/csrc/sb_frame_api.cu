@@ -1,0 +1,176 @@
+// C ABI entry points of the per-frame StyleBlit path (Algorithm 2 and the
+// voting step of Section 3.2): argument validation and kernel dispatch.  The
+// frame kernels live in sb_frame.cuh; the blend kernels are instantiated here.
+#include "sb_frame.cuh"
+
+namespace sb {
+
+static cudaError_t launch_frame_any(int channels, int bits, int mode, const FrameArgs &a,
+                                    cudaStream_t s) {
+    if (bits == 8) {
+        switch (channels) {
+            case 1: return launch_frame_c1b8(mode, a, s);
+            case 2: return launch_frame_c2b8(mode, a, s);
+            case 3: return launch_frame_c3b8(mode, a, s);
+            case 4: return launch_frame_c4b8(mode, a, s);
+        }
+    } else if (bits == 16) {
+        switch (channels) {
+            case 1: return launch_frame_c1b16(mode, a, s);
+            case 2: return launch_frame_c2b16(mode, a, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <bool F32, int R>
+static cudaError_t launch_blend_r(const FrameArgs &a, cudaStream_t s) {
+    return launch_tiles<blend_kernel<F32, R>>(smem_layout(R, 0).total, a.W, a.H, s, a);
+}
+
+template <bool F32>
+static cudaError_t launch_blend(const FrameArgs &a, cudaStream_t s) {
+    switch (a.radius) {
+        case 0: return launch_blend_r<F32, 0>(a, s);
+        case 1: return launch_blend_r<F32, 1>(a, s);
+        case 2: return launch_blend_r<F32, 2>(a, s);
+        case 3: return launch_blend_r<F32, 3>(a, s);
+        case 4: return launch_blend_r<F32, 4>(a, s);
+        case 5: return launch_blend_r<F32, 5>(a, s);
+        case 6: return launch_blend_r<F32, 6>(a, s);
+        case 7: return launch_blend_r<F32, 7>(a, s);
+        case 8: return launch_blend_r<F32, 8>(a, s);
+        case 9: return launch_blend_r<F32, 9>(a, s);
+        case 10: return launch_blend_r<F32, 10>(a, s);
+        case 11: return launch_blend_r<F32, 11>(a, s);
+        case 12: return launch_blend_r<F32, 12>(a, s);
+        case 13: return launch_blend_r<F32, 13>(a, s);
+        case 14: return launch_blend_r<F32, 14>(a, s);
+        case 15: return launch_blend_r<F32, 15>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// validation shared by sb_assign_chunks and sb_stylize
+static sb_status check_frame(const sb_guide *tgt, const sb_guide *src, const sb_lut *lut,
+                             int32_t levels) {
+    sb_status st = check_guide(tgt, "tgt_guide", false);
+    if (st != SB_OK) return st;
+    if ((st = check_guide(src, "src_guide", true)) != SB_OK) return st;
+    if (tgt->channels != src->channels || tgt->bits != src->bits)
+        return fail(SB_ERR_INVALID_ARG, "target and source guides differ in channels or bits");
+    if (!lut) return fail(SB_ERR_INVALID_ARG, "lut: NULL");
+    if (lut->channels != src->channels || lut->bits != src->bits || lut->src_w != src->width ||
+        lut->src_h != src->height)
+        return fail(SB_ERR_INVALID_ARG, "lut was built for a different source guide format/size");
+    if (levels < 1 || levels > kMaxLevels)
+        return fail(SB_ERR_INVALID_ARG, "levels must be in [1, 12]");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != lut->device) return fail(SB_ERR_INVALID_ARG, "lut lives on another device");
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pending CUDA error");
+    return SB_OK;
+}
+
+static FrameArgs frame_args(const sb_guide *tgt, const sb_lut *lut, int32_t levels,
+                            uint64_t threshold, uint32_t seed) {
+    FrameArgs a{};
+    a.tgt = static_cast<const uint8_t *>(tgt->data);
+    a.tgt_stride = tgt->row_stride;
+    a.W = tgt->width;
+    a.H = tgt->height;
+    a.src_packed = lut->src_packed;
+    a.Ws = lut->src_w;
+    a.Hs = lut->src_h;
+    a.lut = lut->entries;
+    a.key_bits = lut->key_bits;
+    a.levels = levels;
+    a.threshold = threshold;
+    a.seed = seed;
+    return a;
+}
+
+}  // namespace sb
+
+using namespace sb;
+
+extern "C" sb_status sb_assign_chunks(const sb_guide *tgt_guide, const sb_guide *src_guide,
+                                      const sb_lut *lut, int32_t levels, uint64_t threshold,
+                                      uint32_t seed, uint32_t *assign_out, uint8_t *level_out,
+                                      sb_stream stream) {
+    sb_status st = check_frame(tgt_guide, src_guide, lut, levels);
+    if (st != SB_OK) return st;
+    if ((int64_t)tgt_guide->width * tgt_guide->height == 0) return ok();
+    if (!assign_out) return fail(SB_ERR_INVALID_ARG, "assign_out: NULL");
+    if ((uintptr_t)assign_out % 4) return fail(SB_ERR_INVALID_ARG, "assign_out: misaligned");
+    FrameArgs a = frame_args(tgt_guide, lut, levels, threshold, seed);
+    a.assign_out = assign_out;
+    a.level_out = level_out;
+    cudaError_t e = launch_frame_any(tgt_guide->channels, tgt_guide->bits, kAssign, a,
+                                     static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "sb_assign_chunks");
+    return ok();
+}
+
+extern "C" sb_status sb_stylize(const sb_guide *tgt_guide, const sb_guide *src_guide,
+                                const sb_rgba8 *src_style, const sb_lut *lut, int32_t levels,
+                                uint64_t threshold, int32_t blend_radius, uint32_t seed,
+                                uint8_t *rgba8_out, sb_stream stream) {
+    sb_status st = check_frame(tgt_guide, src_guide, lut, levels);
+    if (st != SB_OK) return st;
+    if ((st = check_style(src_style, "src_style")) != SB_OK) return st;
+    if (src_style->width != src_guide->width || src_style->height != src_guide->height)
+        return fail(SB_ERR_INVALID_ARG, "src_style and src_guide differ in size");
+    if (blend_radius < 0 || blend_radius > kMaxFusedRadius)
+        return fail(SB_ERR_INVALID_ARG, "blend_radius must be in [0, 7]");
+    if ((int64_t)tgt_guide->width * tgt_guide->height == 0) return ok();
+    if (!rgba8_out || ((uintptr_t)rgba8_out % 4))
+        return fail(SB_ERR_INVALID_ARG, "rgba8_out: NULL or not 4-byte aligned");
+    FrameArgs a = frame_args(tgt_guide, lut, levels, threshold, seed);
+    a.style = src_style->data;
+    a.style_stride = src_style->row_stride;
+    a.radius = blend_radius;
+    a.rgba_out = reinterpret_cast<uint32_t *>(rgba8_out);
+    cudaError_t e = launch_frame_any(tgt_guide->channels, tgt_guide->bits, kStylize, a,
+                                     static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "sb_stylize");
+    return ok();
+}
+
+extern "C" sb_status sb_blend(const uint32_t *assign, int32_t tgt_w, int32_t tgt_h,
+                              const sb_rgba8 *src_style, int32_t blend_radius,
+                              uint8_t *rgba8_out, float *rgba32f_out, sb_stream stream) {
+    sb_status st = check_style(src_style, "src_style");
+    if (st != SB_OK) return st;
+    if (tgt_w < 0 || tgt_h < 0 || tgt_w > kMaxTargetSide || tgt_h > kMaxTargetSide)
+        return fail(SB_ERR_INVALID_ARG, "target size out of range");
+    if (blend_radius < 0 || blend_radius > kMaxBlendRadius)
+        return fail(SB_ERR_INVALID_ARG, "blend_radius must be in [0, 15]");
+    if ((rgba8_out == nullptr) == (rgba32f_out == nullptr))
+        return fail(SB_ERR_INVALID_ARG, "exactly one of rgba8_out / rgba32f_out must be set");
+    if ((int64_t)tgt_w * tgt_h == 0) return ok();
+    if (!assign || ((uintptr_t)assign % 4))
+        return fail(SB_ERR_INVALID_ARG, "assign: NULL or misaligned");
+    if (rgba8_out && ((uintptr_t)rgba8_out % 4))
+        return fail(SB_ERR_INVALID_ARG, "rgba8_out: not 4-byte aligned");
+    if (rgba32f_out && ((uintptr_t)rgba32f_out % 16))
+        return fail(SB_ERR_INVALID_ARG, "rgba32f_out: not 16-byte aligned");
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pending CUDA error");
+    FrameArgs a{};
+    a.W = tgt_w;
+    a.H = tgt_h;
+    a.Ws = src_style->width;
+    a.Hs = src_style->height;
+    a.style = src_style->data;
+    a.style_stride = src_style->row_stride;
+    a.radius = blend_radius;
+    a.assign_in = assign;
+    a.rgba_out = reinterpret_cast<uint32_t *>(rgba8_out);
+    a.f32_out = reinterpret_cast<float4 *>(rgba32f_out);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = rgba32f_out ? launch_blend<true>(a, s) : launch_blend<false>(a, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sb_blend");
+    return ok();
+}

@@ -1,0 +1,8 @@
+// Frame kernels instantiated for 8-bit guides with 1 channel.
+#include "sb_frame.cuh"
+
+namespace sb {
+cudaError_t launch_frame_c1b8(int mode, const FrameArgs &a, cudaStream_t s) {
+    return launch_frame<1, 8>(mode, a, s);
+}
+}  // namespace sb

@@ -1,0 +1,8 @@
+// Frame kernels instantiated for 8-bit guides with 4 channels.
+#include "sb_frame.cuh"
+
+namespace sb {
+cudaError_t launch_frame_c4b8(int mode, const FrameArgs &a, cudaStream_t s) {
+    return launch_frame<4, 8>(mode, a, s);
+}
+}  // namespace sb

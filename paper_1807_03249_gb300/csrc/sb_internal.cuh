@@ -14,6 +14,7 @@
 
 struct sb_lut {
     uint32_t *entries = nullptr;   // device, 2^(channels*key_bits) packed x | y << 16
+    uint32_t *src_packed = nullptr;  // device, the source guide, one packed uint32 per pixel
     int64_t n_entries = 0;
     int32_t channels = 0;
     int32_t bits = 0;
@@ -97,7 +98,11 @@ struct GuideFmt {
 
     // squared Euclidean guide distance; fits 32 bits except 16-bit x 2
     __device__ __forceinline__ static uint64_t dist(uint32_t a, uint32_t b) {
-        if constexpr (B == 8 || C == 1) {
+        if constexpr (B == 8) {
+            // |a - b|^2 = |a|^2 + |b|^2 - 2 a.b with 4-way byte dot products
+            // (unused channels are zero in both); exact in 32 bits
+            return __dp4a(a, a, 0u) + __dp4a(b, b, 0u) - 2u * __dp4a(a, b, 0u);
+        } else if constexpr (C == 1) {
             uint32_t d = 0;
 #pragma unroll
             for (int c = 0; c < C; ++c) {

@@ -23,6 +23,19 @@ namespace sb {
 constexpr int kLutTile = 16;
 constexpr int kLutThreads = 256;
 
+// One packed uint32 per source pixel (the layout GuideFmt::load returns), so
+// later gathers of G_S are single aligned 32-bit loads.
+template <int C, int B>
+__global__ void __launch_bounds__(256) pack_guide_kernel(const uint8_t *__restrict__ src,
+                                                         int64_t stride, int W, int H,
+                                                         uint32_t *__restrict__ packed) {
+    using F = GuideFmt<C, B>;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)W * H) return;
+    const int y = (int)(i / W), x = (int)(i % W);
+    packed[i] = F::load(src, stride, x, y);
+}
+
 template <int C, int B>
 __global__ void __launch_bounds__(256) lut_tile_bounds_kernel(const uint8_t *__restrict__ src,
                                                               int64_t stride, int W, int H,
@@ -84,17 +97,18 @@ __device__ __forceinline__ uint64_t box_distance(const uint32_t (&rep)[C], uint4
 }
 
 template <int C, int B>
-__device__ __forceinline__ void scan_tile(const uint8_t *__restrict__ src, int64_t stride, int W,
-                                          int H, int tiles_x, int t, uint32_t rep_packed,
+__device__ __forceinline__ void scan_tile(const uint32_t *__restrict__ packed, int W, int H,
+                                          int tiles_x, int t, uint32_t rep_packed,
                                           uint64_t &bd, uint32_t &bl) {
     using F = GuideFmt<C, B>;
     const int x0 = (t % tiles_x) * kLutTile;
     const int y0 = (t / tiles_x) * kLutTile;
     const int x1 = min(x0 + kLutTile, W), y1 = min(y0 + kLutTile, H);
     for (int y = y0; y < y1; ++y) {
+        const uint32_t *row = packed + (int64_t)y * W;
 #pragma unroll 4
         for (int x = x0; x < x1; ++x) {
-            const uint64_t d = F::dist(rep_packed, F::load(src, stride, x, y));
+            const uint64_t d = F::dist(rep_packed, __ldg(row + x));
             const uint32_t lin = (uint32_t)y * (uint32_t)W + (uint32_t)x;
             if (d < bd || (d == bd && lin < bl)) {
                 bd = d;
@@ -106,7 +120,7 @@ __device__ __forceinline__ void scan_tile(const uint8_t *__restrict__ src, int64
 
 template <int C, int B>
 __global__ void __launch_bounds__(kLutThreads)
-    lut_search_kernel(const uint8_t *__restrict__ src, int64_t stride, int W, int H, int tiles_x,
+    lut_search_kernel(const uint32_t *__restrict__ packed, int W, int H, int tiles_x,
                       int n_tiles, const uint4 *__restrict__ bounds, int key_bits,
                       uint32_t n_bins, uint32_t *__restrict__ lut) {
     using F = GuideFmt<C, B>;
@@ -117,7 +131,9 @@ __global__ void __launch_bounds__(kLutThreads)
     uint32_t key[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) key[c] = 0;
-    for (int i = 0; i < C * key_bits; ++i) key[i % C] |= ((g >> i) & 1u) << (i / C);
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+        for (int b = 0; b < key_bits; ++b) key[c] |= ((g >> (b * C + c)) & 1u) << b;
     const int z = B - key_bits;
     uint32_t rep[C];
     uint32_t rep_packed = 0, idx = 0;
@@ -141,7 +157,7 @@ __global__ void __launch_bounds__(kLutThreads)
     // pass B: an initial best from that tile
     uint64_t bd = ~0ull;
     uint32_t bl = 0xFFFFFFFFu;
-    scan_tile<C, B>(src, stride, W, H, tiles_x, best_t, rep_packed, bd, bl);
+    scan_tile<C, B>(packed, W, H, tiles_x, best_t, rep_packed, bd, bl);
     // pass C: every tile that could still hold a better or tied-earlier pixel
     for (int t = 0; t < n_tiles; ++t) {
         const uint64_t lb = box_distance<C, B>(rep, __ldg(&bounds[t]));
@@ -149,7 +165,7 @@ __global__ void __launch_bounds__(kLutThreads)
                                (uint32_t)((t % tiles_x) * kLutTile);
         const bool need = valid && (lb < bd || (lb == bd && first < bl));
         if (__any_sync(0xFFFFFFFFu, need))
-            scan_tile<C, B>(src, stride, W, H, tiles_x, t, rep_packed, bd, bl);
+            scan_tile<C, B>(packed, W, H, tiles_x, t, rep_packed, bd, bl);
     }
     if (valid) lut[idx] = (bl % (uint32_t)W) | ((bl / (uint32_t)W) << 16);
 }
@@ -160,6 +176,7 @@ struct LutLaunch {
     uint32_t n_bins;
     uint4 *bounds;
     uint32_t *entries;
+    uint32_t *packed;
     cudaStream_t stream;
     template <int C, int B>
     void operator()() {
@@ -167,12 +184,14 @@ struct LutLaunch {
         const int tiles_y = (src->height + kLutTile - 1) / kLutTile;
         const int n_tiles = tiles_x * tiles_y;
         const uint8_t *p = static_cast<const uint8_t *>(src->data);
+        const int64_t n_px = (int64_t)src->width * src->height;
+        pack_guide_kernel<C, B><<<(unsigned)((n_px + 255) / 256), 256, 0, stream>>>(
+            p, src->row_stride, src->width, src->height, packed);
         lut_tile_bounds_kernel<C, B><<<(n_tiles + 7) / 8, 256, 0, stream>>>(
             p, src->row_stride, src->width, src->height, tiles_x, n_tiles, bounds);
         lut_search_kernel<C, B><<<(n_bins + kLutThreads - 1) / kLutThreads, kLutThreads, 0,
-                                  stream>>>(p, src->row_stride, src->width, src->height,
-                                            tiles_x, n_tiles, bounds, key_bits, n_bins,
-                                            entries);
+                                  stream>>>(packed, src->width, src->height, tiles_x, n_tiles,
+                                            bounds, key_bits, n_bins, entries);
     }
 };
 
@@ -210,19 +229,27 @@ extern "C" sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, s
         delete lut;
         return cuda_fail(e, "sb_build_lut: table allocation");
     }
+    const size_t n_px = (size_t)src_guide->width * src_guide->height;
+    if ((e = cudaMalloc(&lut->src_packed, sizeof(uint32_t) * n_px)) != cudaSuccess) {
+        cudaFree(lut->entries);
+        delete lut;
+        return cuda_fail(e, "sb_build_lut: packed guide allocation");
+    }
     uint4 *bounds = nullptr;
     if ((e = cudaMallocAsync(&bounds, sizeof(uint4) * n_tiles, s)) != cudaSuccess) {
         cudaFree(lut->entries);
+        cudaFree(lut->src_packed);
         delete lut;
         return cuda_fail(e, "sb_build_lut: scratch allocation");
     }
-    LutLaunch L{src_guide, key_bits, n_bins, bounds, lut->entries, s};
+    LutLaunch L{src_guide, key_bits, n_bins, bounds, lut->entries, lut->src_packed, s};
     dispatch_format(src_guide->channels, src_guide->bits, L);
     e = cudaGetLastError();
     cudaFreeAsync(bounds, s);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(s);
         cudaFree(lut->entries);
+        cudaFree(lut->src_packed);
         delete lut;
         return cuda_fail(e, "sb_build_lut: launch");
     }
@@ -233,6 +260,8 @@ extern "C" sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, s
 extern "C" sb_status sb_lut_destroy(sb_lut *lut) {
     if (!lut) return ok();
     cudaError_t e = cudaFree(lut->entries);
+    cudaError_t e2 = cudaFree(lut->src_packed);
+    if (e == cudaSuccess) e = e2;
     delete lut;
     if (e != cudaSuccess) return cuda_fail(e, "sb_lut_destroy");
     return ok();
