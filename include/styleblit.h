@@ -112,6 +112,35 @@ typedef struct sb_lut sb_lut;
 SB_API sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, sb_lut **out,
                        sb_stream stream);
 
+/*
+ * sb_build_lut_noalloc -- the table of sb_build_lut, built into memory the
+ * caller owns, with no device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory, e.g. a
+ * host application whose pool allocator already owns the GPU's memory, or a
+ * frame loop that must not call cudaMalloc (it can synchronise the device and
+ * can fail under memory pressure).
+ *
+ *   src_guide  source guide G_S (device), as for sb_build_lut, at most 65536
+ *              tiles of 16 x 16 pixels (e.g. 4096 x 4096); larger guides are
+ *              rejected with SB_ERR_INVALID_ARG.
+ *   key_bits   as for sb_build_lut.
+ *   table_out  device uint32[2^(channels * key_bits)], 4-byte aligned, owned by
+ *              the caller: receives the same entries sb_build_lut computes.
+ *   stream     the build is enqueued on this stream.
+ * Scratch: a fixed 1 MiB array inside the library (file-scope device memory,
+ * held by every GPU that loads the library until the process exits).  The
+ * first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (every call overwrites what it reads, nothing needs clearing): calls whose
+ * GPU work overlaps (e.g. enqueued on different streams without ordering)
+ * race on it, so serialise them.  Nothing is allocated or freed: no
+ * cudaMalloc, no cudaFree, no allocating library routine.
+ * Errors: SB_ERR_INVALID_ARG, SB_ERR_UNSUPPORTED, SB_ERR_CUDA.
+ */
+SB_API sb_status sb_build_lut_noalloc(const sb_guide *src_guide, int32_t key_bits,
+                                      uint32_t *table_out, sb_stream stream);
+
 /* Frees a table (NULL is a no-op).  The caller must ensure no enqueued work
  * still uses it (e.g. synchronise the streams that used it first). */
 SB_API sb_status sb_lut_destroy(sb_lut *lut);

@@ -32,9 +32,9 @@ SB_OK = 0
 _STATUS = {0: "SB_OK", -1: "SB_ERR_INVALID_ARG", -2: "SB_ERR_UNSUPPORTED", -3: "SB_ERR_CUDA",
            -4: "SB_ERR_OOM", -5: "SB_ERR_TIMEOUT"}
 
-EXPORTED_SYMBOLS = ["sb_build_lut", "sb_lut_destroy", "sb_lut_info", "sb_assign_chunks",
-                    "sb_blend", "sb_stylize", "sb_status_string", "sb_last_error",
-                    "sb_version"]
+EXPORTED_SYMBOLS = ["sb_build_lut", "sb_build_lut_noalloc", "sb_lut_destroy", "sb_lut_info",
+                    "sb_assign_chunks", "sb_blend", "sb_stylize", "sb_status_string",
+                    "sb_last_error", "sb_version"]
 
 
 class StyleBlitError(RuntimeError):
@@ -79,6 +79,7 @@ def load_library(build_if_missing: bool = True):
                                   ctypes.c_uint32, ctypes.c_uint64)
         sigs = {
             "sb_build_lut": (ctypes.c_int, [P(_Guide), i32, P(vp), vp]),
+            "sb_build_lut_noalloc": (ctypes.c_int, [P(_Guide), i32, vp, vp]),
             "sb_lut_destroy": (ctypes.c_int, [vp]),
             "sb_lut_info": (ctypes.c_int, [vp, P(vp), P(i64), P(i32), P(i32), P(i32), P(i32),
                                            P(i32)]),

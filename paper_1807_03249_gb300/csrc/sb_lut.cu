@@ -14,7 +14,9 @@
 //      holds no pixel strictly closer than the best and no tie with a smaller
 //      linear index, so the result equals the brute-force argmin.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
+#include <mutex>
 
 #include "sb_internal.cuh"
 
@@ -96,19 +98,36 @@ __device__ __forceinline__ uint64_t box_distance(const uint32_t (&rep)[C], uint4
     return lb;
 }
 
+// Source-guide readers for the search: the packed copy owned by an sb_lut,
+// or the caller's guide itself (used by the allocation-free build).
+struct PackedReader {
+    const uint32_t *p;
+    int W;
+    __device__ __forceinline__ uint32_t operator()(int x, int y) const {
+        return __ldg(p + (int64_t)y * W + x);
+    }
+};
+
 template <int C, int B>
-__device__ __forceinline__ void scan_tile(const uint32_t *__restrict__ packed, int W, int H,
-                                          int tiles_x, int t, uint32_t rep_packed,
-                                          uint64_t &bd, uint32_t &bl) {
+struct RawReader {
+    const uint8_t *base;
+    int64_t stride;
+    __device__ __forceinline__ uint32_t operator()(int x, int y) const {
+        return GuideFmt<C, B>::load(base, stride, x, y);
+    }
+};
+
+template <int C, int B, typename Reader>
+__device__ __forceinline__ void scan_tile(const Reader &rd, int W, int H, int tiles_x, int t,
+                                          uint32_t rep_packed, uint64_t &bd, uint32_t &bl) {
     using F = GuideFmt<C, B>;
     const int x0 = (t % tiles_x) * kLutTile;
     const int y0 = (t / tiles_x) * kLutTile;
     const int x1 = min(x0 + kLutTile, W), y1 = min(y0 + kLutTile, H);
     for (int y = y0; y < y1; ++y) {
-        const uint32_t *row = packed + (int64_t)y * W;
 #pragma unroll 4
         for (int x = x0; x < x1; ++x) {
-            const uint64_t d = F::dist(rep_packed, __ldg(row + x));
+            const uint64_t d = F::dist(rep_packed, rd(x, y));
             const uint32_t lin = (uint32_t)y * (uint32_t)W + (uint32_t)x;
             if (d < bd || (d == bd && lin < bl)) {
                 bd = d;
@@ -118,16 +137,15 @@ __device__ __forceinline__ void scan_tile(const uint32_t *__restrict__ packed, i
     }
 }
 
-template <int C, int B>
+template <int C, int B, typename Reader>
 __global__ void __launch_bounds__(kLutThreads)
-    lut_search_kernel(const uint32_t *__restrict__ packed, int W, int H, int tiles_x,
-                      int n_tiles, const uint4 *__restrict__ bounds, int key_bits,
-                      uint32_t n_bins, uint32_t *__restrict__ lut) {
-    using F = GuideFmt<C, B>;
+    lut_search_kernel(const Reader rd, int W, int H, int tiles_x, int n_tiles,
+                      const uint4 *__restrict__ bounds, int key_bits, uint32_t n_bins,
+                      uint32_t *__restrict__ lut) {
     const uint32_t g = blockIdx.x * kLutThreads + threadIdx.x;
     const bool valid = g < n_bins;
 
-    // Morton order: bit i of g is bit i / C of channel i % C's key
+    // Morton order: bit b*C + c of g is bit b of channel c's key
     uint32_t key[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) key[c] = 0;
@@ -157,15 +175,14 @@ __global__ void __launch_bounds__(kLutThreads)
     // pass B: an initial best from that tile
     uint64_t bd = ~0ull;
     uint32_t bl = 0xFFFFFFFFu;
-    scan_tile<C, B>(packed, W, H, tiles_x, best_t, rep_packed, bd, bl);
+    scan_tile<C, B>(rd, W, H, tiles_x, best_t, rep_packed, bd, bl);
     // pass C: every tile that could still hold a better or tied-earlier pixel
     for (int t = 0; t < n_tiles; ++t) {
         const uint64_t lb = box_distance<C, B>(rep, __ldg(&bounds[t]));
         const uint32_t first = (uint32_t)((t / tiles_x) * kLutTile) * (uint32_t)W +
                                (uint32_t)((t % tiles_x) * kLutTile);
         const bool need = valid && (lb < bd || (lb == bd && first < bl));
-        if (__any_sync(0xFFFFFFFFu, need))
-            scan_tile<C, B>(packed, W, H, tiles_x, t, rep_packed, bd, bl);
+        if (__any_sync(0xFFFFFFFFu, need)) scan_tile<C, B>(rd, W, H, tiles_x, t, rep_packed, bd, bl);
     }
     if (valid) lut[idx] = (bl % (uint32_t)W) | ((bl / (uint32_t)W) << 16);
 }
@@ -176,7 +193,7 @@ struct LutLaunch {
     uint32_t n_bins;
     uint4 *bounds;
     uint32_t *entries;
-    uint32_t *packed;
+    uint32_t *packed;   // NULL: search the caller's guide directly
     cudaStream_t stream;
     template <int C, int B>
     void operator()() {
@@ -185,13 +202,20 @@ struct LutLaunch {
         const int n_tiles = tiles_x * tiles_y;
         const uint8_t *p = static_cast<const uint8_t *>(src->data);
         const int64_t n_px = (int64_t)src->width * src->height;
-        pack_guide_kernel<C, B><<<(unsigned)((n_px + 255) / 256), 256, 0, stream>>>(
-            p, src->row_stride, src->width, src->height, packed);
+        const unsigned search_blocks = (n_bins + kLutThreads - 1) / kLutThreads;
         lut_tile_bounds_kernel<C, B><<<(n_tiles + 7) / 8, 256, 0, stream>>>(
             p, src->row_stride, src->width, src->height, tiles_x, n_tiles, bounds);
-        lut_search_kernel<C, B><<<(n_bins + kLutThreads - 1) / kLutThreads, kLutThreads, 0,
-                                  stream>>>(packed, src->width, src->height, tiles_x, n_tiles,
-                                            bounds, key_bits, n_bins, entries);
+        if (packed) {
+            pack_guide_kernel<C, B><<<(unsigned)((n_px + 255) / 256), 256, 0, stream>>>(
+                p, src->row_stride, src->width, src->height, packed);
+            lut_search_kernel<C, B><<<search_blocks, kLutThreads, 0, stream>>>(
+                PackedReader{packed, src->width}, src->width, src->height, tiles_x, n_tiles,
+                bounds, key_bits, n_bins, entries);
+        } else {
+            lut_search_kernel<C, B><<<search_blocks, kLutThreads, 0, stream>>>(
+                RawReader<C, B>{p, src->row_stride}, src->width, src->height, tiles_x, n_tiles,
+                bounds, key_bits, n_bins, entries);
+        }
     }
 };
 
@@ -278,5 +302,77 @@ extern "C" sb_status sb_lut_info(const sb_lut *lut, const uint32_t **entries, in
     if (key_bits) *key_bits = lut->key_bits;
     if (src_width) *src_width = lut->src_w;
     if (src_height) *src_height = lut->src_h;
+    return ok();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free table build.
+//
+// Some callers cannot allocate device memory: a host application whose pool
+// allocator already owns the device's memory, or a frame loop that must not
+// call cudaMalloc (it can synchronise the device and fail under memory
+// pressure).  sb_build_lut_noalloc builds the same table into a buffer the
+// caller provides.  Its only scratch, the per-tile guide boxes, lives in the
+// fixed array below, which every GPU that loads this library holds until the
+// process exits; the search reads the caller's guide directly instead of a
+// packed copy.
+// ---------------------------------------------------------------------------
+namespace sb {
+
+constexpr int kStaticBoundsTiles = 65536;  // 1 MiB: 16x16 tiles of a 4096 x 4096 source
+static __device__ __align__(256) uint4 g_static_bounds[kStaticBoundsTiles];
+
+// Device address of g_static_bounds on the current device, looked up once per
+// device (host code cannot use the symbol itself as a device pointer).
+static cudaError_t static_bounds_address(uint4 **out) {
+    constexpr int kMaxDev = 64;
+    static std::atomic<uint4 *> addr[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    uint4 *p = addr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lock(mu);
+        p = addr[dev].load(std::memory_order_relaxed);
+        if (!p) {
+            e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_static_bounds);
+            if (e != cudaSuccess) return e;
+            addr[dev].store(p, std::memory_order_release);
+        }
+    }
+    *out = p;
+    return cudaSuccess;
+}
+
+}  // namespace sb
+
+extern "C" sb_status sb_build_lut_noalloc(const sb_guide *src_guide, int32_t key_bits,
+                                          uint32_t *table_out, sb_stream stream) {
+    sb_status st = check_guide(src_guide, "src_guide", true);
+    if (st != SB_OK) return st;
+    if (key_bits < 1 || key_bits > src_guide->bits)
+        return fail(SB_ERR_INVALID_ARG, "key_bits must be in [1, bits]");
+    if (src_guide->channels * key_bits > kMaxKeyBitsTotal)
+        return fail(SB_ERR_INVALID_ARG, "channels * key_bits must be <= 24");
+    if (!table_out || ((uintptr_t)table_out % 4))
+        return fail(SB_ERR_INVALID_ARG, "table_out: NULL or not 4-byte aligned");
+    const int tiles_x = (src_guide->width + kLutTile - 1) / kLutTile;
+    const int tiles_y = (src_guide->height + kLutTile - 1) / kLutTile;
+    if ((int64_t)tiles_x * tiles_y > kStaticBoundsTiles)
+        return fail(SB_ERR_INVALID_ARG,
+                    "sb_build_lut_noalloc: source guide too large for the fixed scratch "
+                    "(at most 65536 tiles of 16x16 pixels, e.g. 4096 x 4096)");
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "sb_build_lut_noalloc: pending CUDA error");
+    uint4 *bounds = nullptr;
+    if ((e = static_bounds_address(&bounds)) != cudaSuccess)
+        return cuda_fail(e, "sb_build_lut_noalloc: scratch address");
+    const uint32_t n_bins = 1u << (src_guide->channels * key_bits);
+    LutLaunch L{src_guide, key_bits, n_bins, bounds, table_out, nullptr,
+                static_cast<cudaStream_t>(stream)};
+    dispatch_format(src_guide->channels, src_guide->bits, L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "sb_build_lut_noalloc: launch");
     return ok();
 }
