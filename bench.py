@@ -3,12 +3,14 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload 1080p|4k]
                     [--impl reference]
 
-A step stylises one batch of `frames_per_step` distinct target frames of the
-workload (sb_stylize: Algorithm 2 assignment + Section 3.2 vote, one fused
-kernel per frame) against a device-resident exemplar and look-up table.  The
-batch's guides and outputs exceed the L2 cache, so every step reads its
-inputs from HBM.  Steps are replayed from a CUDA graph so host launch
-overhead cannot starve the GPU.  Prints one JSON line on rank 0.
+A step stylises `frames_per_step` distinct target frames of the workload in
+one sb_stylize_batch launch (Algorithm 2 assignment + Section 3.2 vote, fused,
+every tile of every frame in one grid) against a device-resident exemplar and
+look-up table.  The frames' guides and outputs exceed the L2 cache, so every
+step reads its inputs from HBM.  Steps are replayed from a CUDA graph so host
+launch overhead cannot starve the GPU.  The same frames launched one
+sb_stylize per frame are timed too (`per_frame_launch`).  Prints one JSON line
+on rank 0.
 
 --impl reference times the CPU oracle (plain C, all host cores) on a
 bounded sample of the same workload and prints the same JSON line.
@@ -92,7 +94,7 @@ def kernel_source_hash() -> str:
 def profiled_traffic(workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", f"sb_stylize_{workload}_traffic.txt")
+    path = os.path.join(ROOT, "profiles", f"sb_stylize_batch_{workload}_traffic.txt")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -302,23 +304,52 @@ def run_gpu(args):
         if _ < 2:
             lut.destroy()
 
-    def step_calls():
+    batch = [sb.BatchFrame(g_tgt[i], lut, style, w.levels, w.threshold, w.seed + i, out=outs[i])
+             for i in range(FRAMES_PER_STEP)]
+
+    def step_batch():
+        sb.stylize_batch(batch, w.blend_radius, stream=stream)
+
+    def step_frames():
         for i in range(FRAMES_PER_STEP):
             sb.stylize(g_tgt[i], g_src, style, lut, w.levels, w.threshold, w.blend_radius,
                        w.seed + i, out=outs[i], stream=stream)
 
-    # first calls outside capture (per-kernel attribute set-up), then capture
-    with torch.cuda.stream(stream):
-        step_calls()
-    stream.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        step_calls()
-    torch.cuda.synchronize()
+    def capture(fn):
+        # first call outside capture (per-kernel attribute set-up), then capture
+        with torch.cuda.stream(stream):
+            fn()
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            fn()
+        torch.cuda.synchronize()
+        return g
 
+    def time_graph(g, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(steps):
+                g.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        t = e0.elapsed_time(e1)
+        if world > 1:
+            tt = torch.tensor([t], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t
+
+    graph = capture(step_batch)
+    graph_frames = capture(step_frames)
     for _ in range(max(3, args.warmup)):
         with torch.cuda.stream(stream):
             graph.replay()
+            graph_frames.replay()
     torch.cuda.synchronize()
 
     gpu_id = None
@@ -330,39 +361,32 @@ def run_gpu(args):
     sampler = ClockSampler(gpu_id)
     time.sleep(0.3)
 
-    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.synchronize()
     sampler.mark(True)
-    with torch.cuda.stream(stream):
-        e_start.record(stream)
-        for _ in range(args.steps):
-            graph.replay()
-        e_end.record(stream)
-    torch.cuda.synchronize()
+    ms = time_graph(graph, args.steps)
     sampler.mark(False)
-    barrier()
     clocks = sampler.stop()
-    ms = e_start.elapsed_time(e_end)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     ms_per_step = ms / args.steps
     px_step = FRAMES_PER_STEP * H * W
     value = world * px_step * args.steps / (ms / 1e3) / 1e6
+    pf_steps = max(3, min(args.steps, 300))
+    ms_pf = time_graph(graph_frames, pf_steps)
+    per_frame = {"value": world * px_step * pf_steps / (ms_pf / 1e3) / 1e6, "unit": "Mpixel/s",
+                 "ms_per_step": ms_pf / pf_steps, "steps": pf_steps,
+                 "launch": "CUDA graph of frames_per_step sb_stylize kernels (one per frame)"}
 
-    # end to end through the host-buffer call: pinned H2D, stylise, D2H
+    # end to end through the host-buffer call: pinned H2D, stylise, D2H, with
+    # frames spread over three streams so copies in both directions overlap
     host_in = [torch.from_numpy(f.view(np.int16) if f.dtype == np.uint16 else f).pin_memory()
                for f in frames]
     host_out = [torch.empty((H, W, 4), dtype=torch.uint8).pin_memory() for _ in frames]
     staging = [dict() for _ in frames]
+    e2e_streams = [torch.cuda.Stream(dev) for _ in range(3)]
 
     def e2e_step():
         for i in range(FRAMES_PER_STEP):
             sb.stylize_host(host_in[i], g_src, style, lut, w.levels, w.threshold,
                             w.blend_radius, w.seed + i, host_out[i], staging=staging[i],
-                            stream=stream)
+                            stream=e2e_streams[i % 3])
 
     for _ in range(3):
         e2e_step()
@@ -371,8 +395,14 @@ def run_gpu(args):
     x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         x0.record(stream)
+    for st_ in e2e_streams:
+        st_.wait_event(x0)
     for _ in range(args.e2e_steps):
         e2e_step()
+    for st_ in e2e_streams:
+        ev = torch.cuda.Event()
+        ev.record(st_)
+        stream.wait_event(ev)
     with torch.cuda.stream(stream):
         x1.record(stream)
     torch.cuda.synchronize()
@@ -390,8 +420,8 @@ def run_gpu(args):
     hbm = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    kernel_s = (ms_per_step / FRAMES_PER_STEP) / 1e3
-    alg = ab["frame_bytes"] + ab["exemplar_bytes"]
+    kernel_s = ms_per_step / 1e3  # one batch launch per step
+    alg = FRAMES_PER_STEP * ab["frame_bytes"] + ab["exemplar_bytes"]
     achieved = alg / kernel_s / 1e9
     traffic = profiled_traffic(args.workload)
 
@@ -406,19 +436,24 @@ def run_gpu(args):
                                    f"{ex.lut_bits} bits/channel",
                        "l2": f"no flush: each step reads {step_bytes / 2**20:.0f} MiB of "
                              f"distinct guides and outputs (> {L2_BYTES // 2**20} MiB L2)",
-                       "launch": "CUDA graph of frames_per_step sb_stylize kernels",
+                       "launch": "CUDA graph of one sb_stylize_batch launch over all "
+                                 "frames_per_step frames",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": "frame_kernel<...,stylize> (sb_stylize)",
+                         "kernel": "batch_kernel<3,8,2> (sb_stylize_batch)",
                          "peak_source": f"{peak_src} copy bandwidth",
                          "algorithmic_bytes_per_launch": alg,
-                         "frame_only_frac": ab["frame_bytes"] / kernel_s / 1e9 / hbm,
-                         "kernel_us": kernel_s * 1e6},
+                         "frame_only_frac": FRAMES_PER_STEP * ab["frame_bytes"] / kernel_s
+                         / 1e9 / hbm,
+                         "kernel_us": kernel_s * 1e6,
+                         "bytes_rule": "24 frames x (guide in + RGBA8 out) + exemplar "
+                                       "(style + guide + table) once per launch"},
             "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
-                    "api": "stylize_host (pinned host in/out, per frame)"},
-            "gpu_launches": args.steps * FRAMES_PER_STEP,
+                    "api": "stylize_host per frame (pinned host in/out), 3 streams"},
+            "per_frame_launch": per_frame,
+            "gpu_launches": args.steps,
             "lut_build_ms": min(t_lut),
             "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -207,6 +207,39 @@ SB_API sb_status sb_stylize(const sb_guide *tgt_guide, const sb_guide *src_guide
                      uint64_t threshold, int32_t blend_radius, uint32_t seed,
                      uint8_t *rgba8_out, sb_stream stream);
 
+/* One frame of a batch (sb_stylize_batch).  All pointers are device pointers
+ * owned by the caller, as for sb_stylize. */
+typedef struct {
+    sb_guide tgt_guide;        /* target guide G_T of this frame */
+    const sb_lut *lut;         /* table of this frame's exemplar (sb_build_lut) */
+    sb_rgba8 src_style;        /* that exemplar's style C_S (same size as its guide) */
+    int32_t levels;            /* L, 1..12 */
+    uint64_t threshold;        /* t, squared guide distance, <= accepts */
+    uint32_t seed;             /* frame seed of the jitter hash */
+    uint8_t *rgba8_out;        /* tgt h * tgt w * 4 bytes, 4-byte aligned */
+} sb_frame;
+
+/*
+ * sb_stylize_batch -- sb_stylize for many frames in a single launch (the
+ * batched form of Algorithm 2 plus the voting step of Section 3.2).  Frames
+ * may differ in size, exemplar, level count, threshold and seed; they share
+ * the guide format (channels and bits) and the blend radius.  Every frame's
+ * output is bit-identical to sb_stylize on that frame alone.  The tiles of all
+ * frames form one grid, so the GPU starts later frames while the last tiles of
+ * earlier ones finish.
+ *
+ *   frames        host array of n_frames descriptors (read during the call;
+ *                 the device data they point to must stay valid until the
+ *                 stream reaches the batch).
+ *   n_frames      0..128 (0 is a no-op).
+ *   blend_radius  r, 0 <= r <= 7, for every frame.
+ * Allocates nothing.  Errors: SB_ERR_INVALID_ARG (a frame's arguments, as for
+ * sb_stylize; the message names the frame), SB_ERR_UNSUPPORTED (frames with
+ * different guide formats), SB_ERR_CUDA.
+ */
+SB_API sb_status sb_stylize_batch(const sb_frame *frames, int32_t n_frames, int32_t blend_radius,
+                                  sb_stream stream);
+
 /* Static description of a status code. */
 SB_API const char *sb_status_string(sb_status status);
 

@@ -26,15 +26,18 @@ import torch
 from . import _build
 
 __all__ = ["StyleBlitError", "Lut", "build_lut", "assign_chunks", "blend", "stylize",
-           "stylize_host", "library_path", "load_library", "EXPORTED_SYMBOLS", "version"]
+           "stylize_batch", "BatchFrame", "stylize_host", "library_path", "load_library",
+           "EXPORTED_SYMBOLS", "version", "MAX_BATCH"]
+
+MAX_BATCH = 128
 
 SB_OK = 0
 _STATUS = {0: "SB_OK", -1: "SB_ERR_INVALID_ARG", -2: "SB_ERR_UNSUPPORTED", -3: "SB_ERR_CUDA",
            -4: "SB_ERR_OOM", -5: "SB_ERR_TIMEOUT"}
 
 EXPORTED_SYMBOLS = ["sb_build_lut", "sb_build_lut_noalloc", "sb_lut_destroy", "sb_lut_info",
-                    "sb_assign_chunks", "sb_blend", "sb_stylize", "sb_status_string",
-                    "sb_last_error", "sb_version"]
+                    "sb_assign_chunks", "sb_blend", "sb_stylize", "sb_stylize_batch",
+                    "sb_status_string", "sb_last_error", "sb_version"]
 
 
 class StyleBlitError(RuntimeError):
@@ -52,6 +55,12 @@ class _Guide(ctypes.Structure):
 class _Rgba8(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("width", ctypes.c_int32),
                 ("height", ctypes.c_int32), ("row_stride", ctypes.c_int64)]
+
+
+class _Frame(ctypes.Structure):
+    _fields_ = [("tgt_guide", _Guide), ("lut", ctypes.c_void_p), ("src_style", _Rgba8),
+                ("levels", ctypes.c_int32), ("threshold", ctypes.c_uint64),
+                ("seed", ctypes.c_uint32), ("rgba8_out", ctypes.c_void_p)]
 
 
 _lib = None
@@ -88,6 +97,7 @@ def load_library(build_if_missing: bool = True):
             "sb_blend": (ctypes.c_int, [vp, i32, i32, P(_Rgba8), i32, vp, vp, vp]),
             "sb_stylize": (ctypes.c_int, [P(_Guide), P(_Guide), P(_Rgba8), vp, i32, u64, i32,
                                           u32, vp, vp]),
+            "sb_stylize_batch": (ctypes.c_int, [P(_Frame), i32, i32, vp]),
             "sb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "sb_last_error": (ctypes.c_char_p, []),
             "sb_version": (i32, []),
@@ -121,7 +131,11 @@ def _guide(t: torch.Tensor, name: str) -> _Guide:
         raise ValueError(f"{name} must be a CUDA tensor")
     if t.dim() == 2:
         t = t.unsqueeze(-1)
-    if t.dim() != 3 or t.stride(2) != 1 or t.stride(1) != t.shape[2]:
+    if t.dim() != 3:
+        raise ValueError(f"{name} must be [H, W, C]")
+    h, w, c = t.shape
+    # strides of dimensions of size <= 1 carry no layout information
+    if t.numel() and ((c > 1 and t.stride(2) != 1) or (w > 1 and t.stride(1) != c)):
         raise ValueError(f"{name} must be [H, W, C] with contiguous pixels")
     if t.dtype == torch.uint8:
         bits = 8
@@ -129,17 +143,18 @@ def _guide(t: torch.Tensor, name: str) -> _Guide:
         bits = 16
     else:
         raise TypeError(f"{name}: dtype must be uint8 or (u)int16, got {t.dtype}")
-    h, w, c = t.shape
-    return _Guide(t.data_ptr(), w, h, c, bits, t.stride(0) * t.element_size())
+    row = w * c * t.element_size()
+    stride = t.stride(0) * t.element_size() if (h > 1 and t.numel()) else row
+    return _Guide(t.data_ptr(), w, h, c, bits, stride)
 
 
 def _style(t: torch.Tensor, name: str = "style") -> _Rgba8:
     if not t.is_cuda or t.dtype != torch.uint8 or t.dim() != 3 or t.shape[2] != 4:
         raise ValueError(f"{name} must be a CUDA uint8 tensor [H, W, 4]")
-    if t.stride(2) != 1 or t.stride(1) != 4:
-        raise ValueError(f"{name} must have contiguous RGBA pixels")
     h, w, _ = t.shape
-    return _Rgba8(t.data_ptr(), w, h, t.stride(0))
+    if t.stride(2) != 1 or (w > 1 and t.stride(1) != 4):
+        raise ValueError(f"{name} must have contiguous RGBA pixels")
+    return _Rgba8(t.data_ptr(), w, h, t.stride(0) if h > 1 else 4 * w)
 
 
 class _DeviceArray:
@@ -255,6 +270,34 @@ def stylize(tgt_guide, src_guide, style, lut: Lut, levels: int, threshold: int, 
                                         lut.handle, levels, int(threshold), radius,
                                         seed & 0xFFFFFFFF, out.data_ptr(), _stream(stream)))
     return out
+
+
+class BatchFrame:
+    """One frame of stylize_batch: its target guide, exemplar (table + style),
+    level count, threshold, seed and output (allocated when None)."""
+
+    def __init__(self, tgt_guide, lut: "Lut", style, levels: int, threshold: int, seed: int,
+                 out=None):
+        self.tgt_guide, self.lut, self.style = tgt_guide, lut, style
+        self.levels, self.threshold, self.seed = levels, threshold, seed
+        if out is None:
+            H, W = tgt_guide.shape[:2]
+            out = torch.empty((H, W, 4), dtype=torch.uint8, device=tgt_guide.device)
+        self.out = out
+
+
+def stylize_batch(frames, radius: int, stream=None):
+    """Stylises up to MAX_BATCH frames (BatchFrame) in one launch; returns their
+    outputs.  Frames share the guide format and the blend radius."""
+    lib = load_library()
+    frames = list(frames)
+    arr = (_Frame * max(1, len(frames)))()
+    for k, f in enumerate(frames):
+        arr[k] = _Frame(_guide(f.tgt_guide, f"frames[{k}].tgt_guide"), f.lut.handle,
+                        _style(f.style, f"frames[{k}].style"), f.levels, int(f.threshold),
+                        f.seed & 0xFFFFFFFF, f.out.data_ptr())
+    _check("sb_stylize_batch", lib.sb_stylize_batch(arr, len(frames), radius, _stream(stream)))
+    return [f.out for f in frames]
 
 
 def stylize_host(tgt_guide_host: torch.Tensor, src_guide, style, lut: Lut, levels: int,

@@ -611,11 +611,12 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
                            y0, out_tile);
 }
 
+// One 64 x 32 output tile (tile_x, tile_y) of one frame.
 template <int C, int B, int MODE, int R>
-__global__ void __launch_bounds__(kThreads, 3) frame_kernel(const FrameArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void frame_tile(const FrameArgs &a, int tile_x, int tile_y,
+                                           unsigned char *smem) {
     const SmemLayout L = smem_layout(R, a.levels);
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+    const int x0 = tile_x * kTW, y0 = tile_y * kTH;
     uint8_t *bytes = smem + L.off_bytes;
     assign_region<C, B, R>(a, L, x0 - R, y0 - R, smem, MODE == kAssign ? bytes : nullptr);
     const uint32_t *A = reinterpret_cast<const uint32_t *>(smem + L.off_A);
@@ -646,6 +647,41 @@ __global__ void __launch_bounds__(kThreads, 3) frame_kernel(const FrameArgs a) {
             }
         }
     }
+}
+
+template <int C, int B, int MODE, int R>
+__global__ void __launch_bounds__(kThreads, 3) frame_kernel(const FrameArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    frame_tile<C, B, MODE, R>(a, blockIdx.x, blockIdx.y, smem);
+}
+
+// Many frames in one launch: block b stylises tile b - tile_start[k] of the
+// frame k with tile_start[k] <= b < tile_start[k + 1].  Frames may differ in
+// size, exemplar, levels, threshold and seed; they share the guide format and
+// the blend radius.  One launch lets the tiles of later frames fill the SMs
+// while the last tiles of earlier frames finish.
+constexpr int kMaxBatch = 128;
+
+struct BatchArgs {
+    int n;
+    int tile_start[kMaxBatch + 1];
+    int tiles_x[kMaxBatch];
+    FrameArgs f[kMaxBatch];
+};
+
+template <int C, int B, int R>
+__global__ void __launch_bounds__(kThreads, 3) batch_kernel(const __grid_constant__ BatchArgs b) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int t = (int)blockIdx.x;
+    int lo = 0, hi = b.n - 1;  // last frame whose first tile is <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.tile_start[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const FrameArgs a = b.f[lo];  // register copy: field reads become plain operands
+    const int lt = t - b.tile_start[lo];
+    frame_tile<C, B, kStylize, R>(a, lt % b.tiles_x[lo], lt / b.tiles_x[lo], smem);
 }
 
 template <bool F32, int R>
@@ -715,6 +751,31 @@ cudaError_t launch_stylize_r(const FrameArgs &a, cudaStream_t s) {
                                                         a.H, s, a);
 }
 
+template <int C, int B, int R>
+cudaError_t launch_batch_r(const BatchArgs &b, int max_levels, cudaStream_t s) {
+    const size_t smem = smem_layout(R, max_levels).total;
+    cudaError_t e = ensure_smem<batch_kernel<C, B, R>>(smem);
+    if (e != cudaSuccess) return e;
+    batch_kernel<C, B, R><<<b.tile_start[b.n], kThreads, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+// Launches the batch kernel of guide format <C, B> for blend radius r.
+template <int C, int B>
+cudaError_t launch_batch(const BatchArgs &b, int r, int max_levels, cudaStream_t s) {
+    switch (r) {
+        case 0: return launch_batch_r<C, B, 0>(b, max_levels, s);
+        case 1: return launch_batch_r<C, B, 1>(b, max_levels, s);
+        case 2: return launch_batch_r<C, B, 2>(b, max_levels, s);
+        case 3: return launch_batch_r<C, B, 3>(b, max_levels, s);
+        case 4: return launch_batch_r<C, B, 4>(b, max_levels, s);
+        case 5: return launch_batch_r<C, B, 5>(b, max_levels, s);
+        case 6: return launch_batch_r<C, B, 6>(b, max_levels, s);
+        case 7: return launch_batch_r<C, B, 7>(b, max_levels, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 // Launches the frame kernel of guide format <C, B> in the given mode.
 template <int C, int B>
 cudaError_t launch_frame(int mode, const FrameArgs &a, cudaStream_t s) {
@@ -735,6 +796,13 @@ cudaError_t launch_frame(int mode, const FrameArgs &a, cudaStream_t s) {
 }
 
 // per-format launchers, one translation unit each (sb_frame_c<C>b<B>.cu)
+// per-format batch launchers, defined next to the frame launchers
+cudaError_t launch_batch_c1b8(const BatchArgs &b, int r, int max_levels, cudaStream_t s);
+cudaError_t launch_batch_c2b8(const BatchArgs &b, int r, int max_levels, cudaStream_t s);
+cudaError_t launch_batch_c3b8(const BatchArgs &b, int r, int max_levels, cudaStream_t s);
+cudaError_t launch_batch_c4b8(const BatchArgs &b, int r, int max_levels, cudaStream_t s);
+cudaError_t launch_batch_c1b16(const BatchArgs &b, int r, int max_levels, cudaStream_t s);
+cudaError_t launch_batch_c2b16(const BatchArgs &b, int r, int max_levels, cudaStream_t s);
 cudaError_t launch_frame_c1b8(int mode, const FrameArgs &a, cudaStream_t s);
 cudaError_t launch_frame_c2b8(int mode, const FrameArgs &a, cudaStream_t s);
 cudaError_t launch_frame_c3b8(int mode, const FrameArgs &a, cudaStream_t s);

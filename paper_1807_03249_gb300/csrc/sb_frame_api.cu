@@ -1,6 +1,10 @@
 // C ABI entry points of the per-frame StyleBlit path (Algorithm 2 and the
 // voting step of Section 3.2): argument validation and kernel dispatch.  The
 // frame kernels live in sb_frame.cuh; the blend kernels are instantiated here.
+#include <climits>
+#include <cstdio>
+#include <string>
+
 #include "sb_frame.cuh"
 
 namespace sb {
@@ -18,6 +22,24 @@ static cudaError_t launch_frame_any(int channels, int bits, int mode, const Fram
         switch (channels) {
             case 1: return launch_frame_c1b16(mode, a, s);
             case 2: return launch_frame_c2b16(mode, a, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+static cudaError_t launch_batch_any(int channels, int bits, const BatchArgs &b, int r,
+                                    int max_levels, cudaStream_t s) {
+    if (bits == 8) {
+        switch (channels) {
+            case 1: return launch_batch_c1b8(b, r, max_levels, s);
+            case 2: return launch_batch_c2b8(b, r, max_levels, s);
+            case 3: return launch_batch_c3b8(b, r, max_levels, s);
+            case 4: return launch_batch_c4b8(b, r, max_levels, s);
+        }
+    } else if (bits == 16) {
+        switch (channels) {
+            case 1: return launch_batch_c1b16(b, r, max_levels, s);
+            case 2: return launch_batch_c2b16(b, r, max_levels, s);
         }
     }
     return cudaErrorInvalidValue;
@@ -172,5 +194,65 @@ extern "C" sb_status sb_blend(const uint32_t *assign, int32_t tgt_w, int32_t tgt
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     e = rgba32f_out ? launch_blend<true>(a, s) : launch_blend<false>(a, s);
     if (e != cudaSuccess) return cuda_fail(e, "sb_blend");
+    return ok();
+}
+
+extern "C" sb_status sb_stylize_batch(const sb_frame *frames, int32_t n_frames,
+                                      int32_t blend_radius, sb_stream stream) {
+    if (n_frames < 0 || n_frames > kMaxBatch)
+        return fail(SB_ERR_INVALID_ARG, "n_frames must be in [0, 128]");
+    if (n_frames == 0) return ok();
+    if (!frames) return fail(SB_ERR_INVALID_ARG, "frames: NULL");
+    if (blend_radius < 0 || blend_radius > kMaxFusedRadius)
+        return fail(SB_ERR_INVALID_ARG, "blend_radius must be in [0, 7]");
+    static thread_local BatchArgs b;  // ~18 KB: kept off the stack
+    b.n = n_frames;
+    b.tile_start[0] = 0;
+    int max_levels = 1;
+    const int channels = frames[0].tgt_guide.channels, bits = frames[0].tgt_guide.bits;
+    char name[64];
+    for (int k = 0; k < n_frames; ++k) {
+        const sb_frame &f = frames[k];
+        std::snprintf(name, sizeof name, "frames[%d].tgt_guide", k);
+        sb_status st = check_guide(&f.tgt_guide, name, false);
+        if (st != SB_OK) return st;
+        if (f.tgt_guide.channels != channels || f.tgt_guide.bits != bits)
+            return fail(SB_ERR_UNSUPPORTED, "sb_stylize_batch: frames must share one guide format");
+        std::snprintf(name, sizeof name, "frames[%d]", k);
+        if (!f.lut) return fail(SB_ERR_INVALID_ARG, std::string(name) + ": lut NULL");
+        if (f.lut->channels != channels || f.lut->bits != bits)
+            return fail(SB_ERR_INVALID_ARG, std::string(name) + ": lut built for another format");
+        std::snprintf(name, sizeof name, "frames[%d].src_style", k);
+        if ((st = check_style(&f.src_style, name)) != SB_OK) return st;
+        if (f.src_style.width != f.lut->src_w || f.src_style.height != f.lut->src_h)
+            return fail(SB_ERR_INVALID_ARG, std::string(name) + ": size differs from the lut's guide");
+        if (f.levels < 1 || f.levels > kMaxLevels)
+            return fail(SB_ERR_INVALID_ARG, std::string(name) + ": levels must be in [1, 12]");
+        const int64_t npx = (int64_t)f.tgt_guide.width * f.tgt_guide.height;
+        if (npx > 0 && (!f.rgba8_out || ((uintptr_t)f.rgba8_out % 4)))
+            return fail(SB_ERR_INVALID_ARG, std::string(name) + ": rgba8_out NULL or misaligned");
+        const int tx = (f.tgt_guide.width + kTW - 1) / kTW, ty = (f.tgt_guide.height + kTH - 1) / kTH;
+        const int64_t next = (int64_t)b.tile_start[k] + (npx > 0 ? (int64_t)tx * ty : 0);
+        if (next > INT_MAX) return fail(SB_ERR_INVALID_ARG, "sb_stylize_batch: too many tiles");
+        b.tile_start[k + 1] = (int)next;
+        b.tiles_x[k] = tx > 0 ? tx : 1;
+        FrameArgs a = frame_args(&f.tgt_guide, f.lut, f.levels, f.threshold, f.seed);
+        a.style = f.src_style.data;
+        a.style_stride = f.src_style.row_stride;
+        a.radius = blend_radius;
+        a.rgba_out = reinterpret_cast<uint32_t *>(f.rgba8_out);
+        b.f[k] = a;
+        max_levels = max(max_levels, (int)f.levels);
+    }
+    if (b.tile_start[n_frames] == 0) return ok();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (int k = 0; k < n_frames; ++k)
+        if (frames[k].lut->device != dev) return fail(SB_ERR_INVALID_ARG, "a lut lives on another device");
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pending CUDA error");
+    e = launch_batch_any(channels, bits, b, blend_radius, max_levels,
+                         static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "sb_stylize_batch");
     return ok();
 }

@@ -5,4 +5,7 @@ namespace sb {
 cudaError_t launch_frame_c3b8(int mode, const FrameArgs &a, cudaStream_t s) {
     return launch_frame<3, 8>(mode, a, s);
 }
+cudaError_t launch_batch_c3b8(const BatchArgs &b, int r, int max_levels, cudaStream_t s) {
+    return launch_batch<3, 8>(b, r, max_levels, s);
+}
 }  // namespace sb
