@@ -61,7 +61,7 @@ def make_workload(name: str, n_frames: int, rank: int = 0):
     """Exemplar + `n_frames` distinct target guides (a few generated fields,
     each shifted cyclically by seeded offsets)."""
     base = 3 if name == "1080p" else 2
-    seed0 = (2000 if name == "1080p" else 3000) + 100 * rank
+    seed0 = rank_frame_seed(name, rank)
     w = synth.workload_1080p(base, seed0) if name == "1080p" else synth.workload_4k_uv(base, seed0)
     rng = np.random.default_rng(seed0)
     frames = []
@@ -70,6 +70,28 @@ def make_workload(name: str, n_frames: int, rank: int = 0):
         dy, dx = int(rng.integers(0, g.shape[0])), int(rng.integers(0, g.shape[1]))
         frames.append(np.ascontiguousarray(np.roll(g, (dy, dx), axis=(0, 1))))
     return w, frames
+
+
+def rank_frame_seed(name: str, rank: int) -> int:
+    """Seed of rank `rank`'s frames: ranks stylise disjoint frames (weak
+    scaling; frames are independent, so there is no data-path exchange)."""
+    return (2000 if name == "1080p" else 3000) + 100 * rank
+
+
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time (the job ends when every rank has finished)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, px_per_step_per_rank: int, steps: int, ms: float) -> float:
+    """Whole-job Mpixel/s: every rank's pixels over the slowest rank's time."""
+    return world * px_per_step_per_rank * steps / (ms / 1e3) / 1e6
 
 
 def algorithmic_bytes(w, frame) -> dict:
@@ -192,42 +214,55 @@ class ClockSampler:
 # CPU oracle baseline
 # ---------------------------------------------------------------------------
 
-def cpu_oracle_run(w, frames, budget_s: float = 12.0, steps: int | None = None):
-    """Times the oracle (assignment + RGBA8 vote) on a band of rows of the
-    workload's frames with every host core; look-up table entries the band
-    needs are filled in an untimed pass first (the GPU also runs with a
-    resident table)."""
+def cpu_oracle_run(w, frames, steps: int = 0, warmup: int = 1, budget_s: float = 12.0):
+    """Times the oracle (assignment + RGBA8 vote, every host core) on bands of
+    rows of the workload's frames.  Table entries a band needs are filled in
+    untimed warm-up passes first (the GPU also runs with a resident table).
+    steps > 0: `warmup` untimed then `steps` timed bands, the band height
+    chosen so the timed part takes about `budget_s`; steps == 0: as many
+    64-row bands as fit in `budget_s`."""
     import oracle
     ex = w.exemplar
     cores = os.cpu_count() or 1
     lut = oracle.new_lut(ex.guide.shape[2], ex.lut_bits)
-    rows = 64
-    band = [np.ascontiguousarray(f[:rows]) for f in frames[:2]]
-    for i, g in enumerate(band):  # untimed: fill the table entries the band needs
-        oracle.assign(g, ex.guide, ex.lut_bits, w.levels, w.threshold, w.seed + i, lut=lut,
-                      n_threads=cores)
-    times, px = [], 0
-    t_start = time.perf_counter()
-    n = 0
-    while True:
-        g = band[n % len(band)]
+    full = [np.ascontiguousarray(f) for f in frames[:2]]
+
+    n_bands = 4  # a fixed set of bands: the warm-up fills every table entry they need
+
+    def run_band(k, rows):
+        g = full[k % len(full)]
+        y0 = ((k % n_bands) * (g.shape[0] // n_bands)) % max(1, g.shape[0] - rows + 1)
+        band = np.ascontiguousarray(g[y0:y0 + rows])
         t = time.perf_counter()
-        a, _ = oracle.assign(g, ex.guide, ex.lut_bits, w.levels, w.threshold, w.seed + n % 2,
+        a, _ = oracle.assign(band, ex.guide, ex.lut_bits, w.levels, w.threshold, w.seed + k % 2,
                              lut=lut, n_threads=cores)
         oracle.blend_rgba8(a, ex.style, w.blend_radius, n_threads=cores)
-        times.append(time.perf_counter() - t)
-        px += g.shape[0] * g.shape[1]
+        return time.perf_counter() - t, band.shape[0] * band.shape[1]
+
+    for k in range(max(n_bands, warmup)):  # untimed: fills the table entries bands need
+        run_band(k, 64)
+    t64, _ = run_band(0, 64)  # table resident now: time of one 64-row band
+    rows = 64
+    if steps > 0:
+        rows = int(max(1, min(64, 64 * budget_s / max(1e-9, steps * t64))))
+    times, px, n = [], 0, 0
+    t_start = time.perf_counter()
+    while True:
+        dt, p = run_band(n, rows)
+        times.append(dt)
+        px += p
         n += 1
-        if steps is not None and n >= steps:
+        if steps > 0 and n >= steps:
             break
-        if steps is None and time.perf_counter() - t_start > budget_s:
+        if steps == 0 and time.perf_counter() - t_start > budget_s:
             break
     total = sum(times)
     return {"value": px / total / 1e6, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} x {rows}-row bands ({rows}x{band[0].shape[1]} px) of the "
-                      f"{w.name} frames, assignment + r={w.blend_radius} vote, "
-                      f"table entries filled in an untimed pass",
-            "seconds": total}
+            "sample": f"{n} steps over {n_bands} fixed bands of {rows} rows x "
+                      f"{full[0].shape[1]} px of the {w.name} "
+                      f"frames, assignment + r={w.blend_radius} vote, table entries filled "
+                      f"in untimed warm-up passes",
+            "seconds": total, "ms_per_step": 1e3 * total / n, "steps": n}
 
 
 def run_reference(args):
@@ -235,15 +270,16 @@ def run_reference(args):
     if rank != 0:
         return
     w, frames = make_workload(args.workload, 2)
-    r = cpu_oracle_run(w, frames, steps=None, budget_s=max(5.0, min(60.0, 0.5 * args.steps)))
+    r = cpu_oracle_run(w, frames, steps=args.steps, warmup=args.warmup, budget_s=90.0)
     H, W = frames[0].shape[:2]
     line = {"metric": METRIC, "value": r["value"], "unit": "Mpixel/s", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": w.name, "frame": f"{W}x{H}", "levels": w.levels,
                        "threshold": w.threshold, "blend": f"{2 * w.blend_radius + 1}x"
-                       f"{2 * w.blend_radius + 1}"},
+                       f"{2 * w.blend_radius + 1}",
+                       "step": "one band of rows of a frame (see cpu_baseline.sample)"},
             "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": r["value"], "unit": "Mpixel/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -337,12 +373,7 @@ def run_gpu(args):
             e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        t = e0.elapsed_time(e1)
-        if world > 1:
-            tt = torch.tensor([t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        return t
+        return max_over_ranks(e0.elapsed_time(e1), world, dev)
 
     graph = capture(step_batch)
     graph_frames = capture(step_frames)
@@ -367,10 +398,10 @@ def run_gpu(args):
     clocks = sampler.stop()
     ms_per_step = ms / args.steps
     px_step = FRAMES_PER_STEP * H * W
-    value = world * px_step * args.steps / (ms / 1e3) / 1e6
+    value = job_throughput(world, px_step, args.steps, ms)
     pf_steps = max(3, min(args.steps, 300))
     ms_pf = time_graph(graph_frames, pf_steps)
-    per_frame = {"value": world * px_step * pf_steps / (ms_pf / 1e3) / 1e6, "unit": "Mpixel/s",
+    per_frame = {"value": job_throughput(world, px_step, pf_steps, ms_pf), "unit": "Mpixel/s",
                  "ms_per_step": ms_pf / pf_steps, "steps": pf_steps,
                  "launch": "CUDA graph of frames_per_step sb_stylize kernels (one per frame)"}
 
@@ -407,12 +438,8 @@ def run_gpu(args):
         x1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = x0.elapsed_time(x1)
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e_value = world * px_step * args.e2e_steps / (ms_e2e / 1e3) / 1e6
+    ms_e2e = max_over_ranks(x0.elapsed_time(x1), world, dev)
+    e2e_value = job_throughput(world, px_step, args.e2e_steps, ms_e2e)
     h2d = sum(f.nbytes for f in frames)
     d2h = sum(o.numel() for o in host_out)
 
