@@ -447,7 +447,8 @@ __device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const uint32_
         const uint32_t c = row[col];
         const uint32_t v = c - (uint32_t)((col - tx - R) + (oy << 16));
         const uint32_t vx = v & 0xFFFFu, vy = v >> 16;
-        const bool ok = len != 0u && c != kInvalid && vx < (uint32_t)a.Ws && vy < (uint32_t)a.Hs;
+        // an out-of-target tap (kInvalid) lands out of the source here
+        const bool ok = len != 0u && vx < (uint32_t)a.Ws && vy < (uint32_t)a.Hs;
         const uint32_t colr = ok ? __ldg(style32 + (int64_t)vy * sstride + vx) : 0u;
         acc.add(colr, ok ? len : 0u);
     };
@@ -528,7 +529,7 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
                 bool bit = false;
                 if (x >= 1 && x < RW) {
                     const uint32_t cur = row[x], prv = row[x - 1];
-                    bit = cur != kInvalid && prv != kInvalid && cur == prv + 1u;
+                    bit = cur == prv + 1u;  // never true next to kInvalid
                 }
                 e[c] = __ballot_sync(0xFFFFFFFFu, bit);
             }
@@ -543,7 +544,7 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
                 bool bit = false;
                 if (ry >= 1) {
                     const uint32_t cur = row[x], up = row[x - RW];
-                    bit = cur != kInvalid && up != kInvalid && cur == up + 0x10000u;
+                    bit = cur == up + 0x10000u;
                 }
                 v[c] = __ballot_sync(0xFFFFFFFFu, bit);
             }
@@ -567,10 +568,11 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
         const int ty = warp + q * kWarps;
         uint64_t U = ~0ull;
         if constexpr (R > 0) {
-#pragma unroll
-            for (int kk = 0; kk <= 2 * R; ++kk) U &= hu_row[ty + kk];
-#pragma unroll
-            for (int kk = 1; kk <= 2 * R; ++kk) U &= v_row[ty + kk];
+            // lane j < 2R + 1 brings window row ty + j; one AND-reduction per half
+            uint64_t m = ~0ull;
+            if (lane <= 2 * R) m = hu_row[ty + lane] & (lane > 0 ? v_row[ty + lane] : ~0ull);
+            U = (uint64_t)__reduce_and_sync(0xFFFFFFFFu, (uint32_t)m) |
+                ((uint64_t)__reduce_and_sync(0xFFFFFFFFu, (uint32_t)(m >> 32)) << 32);
         }
 #pragma unroll
         for (int c = 0; c < 2; ++c) {

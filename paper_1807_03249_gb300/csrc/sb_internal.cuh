@@ -26,7 +26,11 @@ struct sb_lut {
 
 namespace sb {
 
-constexpr uint32_t kInvalid = 0xFFFFFFFFu;   // no source position (outside the target)
+// No source position (a pixel outside the target).  Its x field (0xC000) stays
+// above every valid coordinate (< 32767) after subtracting any window offset
+// (|o| <= 15) without a borrow, so A - o of this value is always out of the
+// source and never equals a valid A + o: no separate test is needed.
+constexpr uint32_t kInvalid = 0xC000C000u;
 constexpr int kMaxSourceSide = 32767;         // keeps packed-position arithmetic carry-free
 constexpr int kMaxTargetSide = 65535;
 constexpr int kMaxLevels = 12;
