@@ -219,6 +219,104 @@ __device__ __forceinline__ int4 nearest_cell(const int4 *cells, int base, int c0
     return cl;
 }
 
+// Top level over horizontal pixel pairs (x even, x + 1): the two pixels share
+// their cell at every level, so one pass over the nine candidates gives both
+// packed keys (the right key is the left key plus the candidate's x slope).
+// Accepted pixels get A (and the level); rejected ones are appended to list_out.
+template <int C, int B, int R>
+__device__ __forceinline__ void top_level_pairs(const FrameArgs &a, const uint32_t *gt,
+                                                uint32_t *A, uint8_t *lev, const int4 *cells,
+                                                const LevelCells &g, int l, int rx0, int ry0,
+                                                uint32_t t32, uint16_t *list_out,
+                                                int *cnt_out) {
+    using F = GuideFmt<C, B>;
+    constexpr int RW = kTW + 2 * R, RH = kTH + 2 * R;
+    constexpr int PR = RW / 2 + (R & 1);  // pairs per region row (x0 - R is odd for odd R)
+    constexpr int NP = PR * RH;
+    constexpr int kPairs = 2;             // pairs per thread per batch
+    constexpr int kPx = 2 * kPairs;
+    for (int j0 = 0; j0 < NP; j0 += kThreads * kPairs) {
+        int idx[kPx];
+        uint32_t sv[kPx], gsv[kPx];
+        bool act[kPx], inb[kPx];
+#pragma unroll
+        for (int u = 0; u < kPairs; ++u) {
+            const int jp = j0 + u * kThreads + threadIdx.x;
+            const int ry = jp / PR, rxl = 2 * (jp - ry * PR) - (R & 1);
+            const int il = ry * RW + rxl;
+            bool aL = false, aR = false;
+            if (jp < NP) {
+                aL = rxl >= 0 && A[il] == kPending;
+                aR = rxl + 1 < RW && A[il + 1] == kPending;
+            }
+            act[2 * u] = aL;
+            act[2 * u + 1] = aR;
+            idx[2 * u] = aL ? il : 0;
+            idx[2 * u + 1] = aR ? il + 1 : 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                inb[2 * u + h] = false;
+                gsv[2 * u + h] = 0;
+                sv[2 * u + h] = 0;
+            }
+            if (aL || aR) {
+                const int prl = rxl - RW / 2, pry = ry - RH / 2;
+                // both pixels lie in the cell of the right one's column
+                const int lcx = ((rx0 + rxl + 1) >> l) - g.cx0, lcy = ((ry0 + ry) >> l) - g.cy0;
+                const int c0 = lcx * g.ncy + lcy;
+                int kl = INT_MAX, kr = INT_MAX;
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+#pragma unroll
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        const int4 cl = cells[c0 + dx * g.ncy + dy];
+                        const int e = cl.z + cl.x * prl + cl.y * pry;
+                        kl = min(kl, e);
+                        kr = min(kr, e + cl.x);
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!(h ? aR : aL)) continue;
+                    const int4 cl = cells[(h ? kr : kl) & ((1 << kKeyShift) - 1)];
+                    int sx = (int)((uint32_t)cl.w & 0xFFFFu) + prl + h + (cl.x >> (kKeyShift + 1));
+                    int sy = (int)((uint32_t)cl.w >> 16) + pry + (cl.y >> (kKeyShift + 1));
+                    if (l > 1) {
+                        inb[2 * u + h] =
+                            (unsigned)sx < (unsigned)a.Ws && (unsigned)sy < (unsigned)a.Hs;
+                        if (inb[2 * u + h])
+                            gsv[2 * u + h] = __ldg(a.src_packed + (int64_t)sy * a.Ws + sx);
+                    } else {
+                        sx = min(max(sx, 0), a.Ws - 1);
+                        sy = min(max(sy, 0), a.Hs - 1);
+                    }
+                    sv[2 * u + h] = (uint32_t)sx | ((uint32_t)sy << 16);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kPx; ++k) {
+            bool acc = false;
+            if (act[k]) {
+                if (l > 1) {
+                    if (inb[k]) {
+                        const uint64_t d = F::dist(gsv[k], gt[idx[k]]);
+                        if constexpr (B == 8) acc = (uint32_t)d <= t32;
+                        else acc = d <= a.threshold;
+                    }
+                } else {
+                    acc = true;
+                }
+                if (acc) {
+                    A[idx[k]] = sv[k];
+                    if (lev) lev[idx[k]] = (uint8_t)l;
+                }
+            }
+            list_push(act[k] && !acc, idx[k], list_out, cnt_out);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // assignment of the region held in shared memory (Algorithm 2)
 // ---------------------------------------------------------------------------
@@ -259,7 +357,19 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     int cur = 0;
     int n_pend = NR;  // the top level scans the whole region
     int base = 0;     // first cell of the current level
-    for (int l = L_top; l >= 1 && n_pend > 0; --l) {
+    int l_start = L_top;
+    if (L_top <= kPackedMaxLevel) {
+        // top level by pixel pairs (cells of the top level start at 0)
+        const LevelCells g = level_cells(L_top, xa, xb, ya, yb);
+        top_level_pairs<C, B, R>(a, gt, A, lev, cells, g, L_top, rx0, ry0, t32, list1, &cnt[1]);
+        __syncthreads();
+        n_pend = cnt[1];
+        base = g.ncx * g.ncy;
+        cur = 1;
+        l_start = L_top - 1;
+        __syncthreads();  // every thread has read cnt[1] before the next level writes cnt[0]
+    }
+    for (int l = l_start; l >= 1 && n_pend > 0; --l) {
         const LevelCells g = level_cells(l, xa, xb, ya, yb);
         if (l == kEagerMinLevel - 1 && eager_lo > 1) {
             // a pixel still needs the fine levels: build levels 2 and 1 now
