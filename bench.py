@@ -50,6 +50,9 @@ def _args():
     p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-once", action="store_true",
+                   help="build the step's frames and launch sb_stylize_batch twice, no timing "
+                        "(a fixed launch sequence for ncu captures)")
     return p.parse_args()
 
 
@@ -493,8 +496,32 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def profile_once(args):
+    import torch
+
+    import paper_1807_03249_gb300 as sb
+    dev = torch.device("cuda:0")
+    w, frames = make_workload(args.workload, FRAMES_PER_STEP)
+    ex = w.exemplar
+
+    def to_dev(a):
+        return torch.from_numpy(a.view(np.int16) if a.dtype == np.uint16 else a).to(dev)
+
+    gs, st = to_dev(ex.guide), to_dev(ex.style)
+    lut = sb.build_lut(gs, ex.lut_bits)
+    batch = [sb.BatchFrame(to_dev(f), lut, st, w.levels, w.threshold, w.seed + i)
+             for i, f in enumerate(frames)]
+    for _ in range(2):
+        sb.stylize_batch(batch, w.blend_radius)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_once": w.name, "frames": len(batch)}))
+
+
 def main():
     args = _args()
+    if args.profile_once:
+        profile_once(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
