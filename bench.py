@@ -50,6 +50,7 @@ def _args():
     p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-served", action="store_true")
     p.add_argument("--profile-once", action="store_true",
                    help="build the step's frames and launch sb_stylize_batch twice, no timing "
                         "(a fixed launch sequence for ncu captures)")
@@ -486,6 +487,8 @@ def run_gpu(args):
             "gpu_launches": args.steps,
             "lut_build_ms": min(t_lut),
             "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_served:
+        line["served"] = run_served(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = cpu_oracle_run(w, frames)
         line["cpu_baseline"] = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -494,6 +497,52 @@ def run_gpu(args):
     lut.destroy()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_served(dev, n_requests: int = 10000, rate_hz: float = 2000.0, pool: int = 64,
+               seed: int = 5000) -> dict:
+    """The served workload: a seeded Poisson stream of stylisation requests,
+    frame sizes log-uniform in [256^2, 3840x2160], 16 resident 1024^2
+    exemplars, 40 GB admission budget, 5x5 blend, L=6, T=300.  Request guides
+    are crops of one generated 3840x2160 normal field held in a pool of pinned
+    buffers (outputs of the same pool entry are overwritten; they are not
+    checked here -- tests/test_gpu_serve.py checks served results)."""
+    import torch
+
+    from paper_1807_03249_gb300.serve import Request, Server, latency_summary
+    srv = Server(dev, radius=2, budget_bytes=40 << 30, slots=4, max_batch=16)
+    for k in range(16):
+        ex = synth.normal_exemplar(5100 + k, 1024, strokes=100, lut_bits=6)
+        srv.add_exemplar(k, ex.guide, ex.style, ex.lut_bits)
+    field = synth.bump_normals(seed, 2160, 3840, 96, (20.0, 200.0))
+    sizes = synth.log_uniform_sizes(seed + 1, pool)
+    rng = np.random.default_rng(seed + 2)
+    guides, outs = [], []
+    for (w_, h_) in sizes:
+        y0, x0 = int(rng.integers(0, 2160 - h_ + 1)), int(rng.integers(0, 3840 - w_ + 1))
+        guides.append(torch.from_numpy(np.ascontiguousarray(field[y0:y0 + h_, x0:x0 + w_]))
+                      .pin_memory())
+        outs.append(torch.empty((h_, w_, 4), dtype=torch.uint8).pin_memory())
+    arrivals = synth.poisson_arrivals(seed + 3, rate_hz, n_requests)
+    exs = rng.integers(0, 16, n_requests)
+    seeds = rng.integers(0, 2**32, n_requests)
+
+    def make(i, t0):
+        return Request(i, float(arrivals[i] - t0), int(exs[i]), guides[i % pool], 6, 300,
+                       int(seeds[i]), out=outs[i % pool])
+
+    warm = [make(i, arrivals[0]) for i in range(64)]
+    srv.run(warm, real_time=False)
+    reqs = [make(i, arrivals[0]) for i in range(n_requests)]
+    done, wall = srv.run(reqs, real_time=True)
+    out = latency_summary(done, wall)
+    offered_px = sum(r.pixels for r in reqs) / float(arrivals[-1] - arrivals[0])
+    out.update({"offered_req_per_s": rate_hz, "offered_mpixel_per_s": offered_px / 1e6,
+                "slots": 4, "max_batch": 16, "budget_gb": 40,
+                "peak_admitted_mb": srv.sched.peak_in_use / 1e6,
+                "workload": "Poisson 2000 req/s, log-uniform 256^2..3840x2160 normals, "
+                            "16 resident 1024^2 exemplars, L6 T300 5x5"})
+    return out
 
 
 def profile_once(args):
