@@ -405,6 +405,20 @@ def run_gpu(args):
     value = job_throughput(world, px_step, args.steps, ms)
     pf_steps = max(3, min(args.steps, 300))
     ms_pf = time_graph(graph_frames, pf_steps)
+
+    # the lookup-only comparator (Section 4, texture mapping) on the same frames
+    def step_lookup():
+        for i in range(FRAMES_PER_STEP):
+            sb.lookup_only(g_tgt[i], g_src, style, lut, out=outs[i], stream=stream)
+
+    graph_lookup = capture(step_lookup)
+    ms_lk = time_graph(graph_lookup, pf_steps)
+    lk_bytes = FRAMES_PER_STEP * ab["frame_bytes"]
+    lookup = {"value": job_throughput(world, px_step, pf_steps, ms_lk), "unit": "Mpixel/s",
+              "ms_per_step": ms_lk / pf_steps,
+              "hbm_frac": lk_bytes / (ms_lk / pf_steps / 1e3) / 1e9 /
+              (measured_peaks().get("hbm_gbs") or 6800.0),
+              "what": "C_T[p] = C_S[LUT(G_T[p])] per pixel, one lookup_kernel per frame"}
     per_frame = {"value": job_throughput(world, px_step, pf_steps, ms_pf), "unit": "Mpixel/s",
                  "ms_per_step": ms_pf / pf_steps, "steps": pf_steps,
                  "launch": "CUDA graph of frames_per_step sb_stylize kernels (one per frame)"}
@@ -484,6 +498,7 @@ def run_gpu(args):
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                     "api": "stylize_host per frame (pinned host in/out), 3 streams"},
             "per_frame_launch": per_frame,
+            "lookup_only": lookup,
             "gpu_launches": args.steps,
             "lut_build_ms": min(t_lut),
             "clocks": clocks}

@@ -240,6 +240,20 @@ typedef struct {
 SB_API sb_status sb_stylize_batch(const sb_frame *frames, int32_t n_frames, int32_t blend_radius,
                                   sb_stream stream);
 
+/*
+ * sb_lookup_only -- the per-pixel mapping StyleBlit is compared with in
+ * Section 4 (texture mapping; The Lit Sphere): every target pixel copies the
+ * style at the table entry of its own guide value, C_T[p] = C_S[LUT(G_T[p])],
+ * with no seeds, chunks or vote.  A throughput and quality comparator.
+ *
+ *   tgt_guide, src_guide, src_style, lut: as sb_stylize.
+ *   rgba8_out  device uint8[tgt h * tgt w * 4], 4-byte aligned.
+ * Errors: SB_ERR_INVALID_ARG, SB_ERR_UNSUPPORTED, SB_ERR_CUDA.
+ */
+SB_API sb_status sb_lookup_only(const sb_guide *tgt_guide, const sb_guide *src_guide,
+                                const sb_rgba8 *src_style, const sb_lut *lut, uint8_t *rgba8_out,
+                                sb_stream stream);
+
 /* Static description of a status code. */
 SB_API const char *sb_status_string(sb_status status);
 

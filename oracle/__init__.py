@@ -83,6 +83,7 @@ def _load():
                 "orc_blend_f32": (ctypes.c_int, [vp, i32, i32, P(_Rgba8), i32, vp, i32]),
                 "orc_stylize_points": (ctypes.c_int, [P(_Guide), P(_Guide), P(_Rgba8), i32, vp,
                                                       i32, u64, i32, u32, vp, vp, i64, vp]),
+                "orc_lookup_only": (ctypes.c_int, [P(_Guide), P(_Guide), P(_Rgba8), i32, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -259,4 +260,17 @@ def stylize_points(tgt_guide, src_guide, style, key_bits, levels, threshold, rad
     _load().orc_stylize_points(ctypes.byref(t), ctypes.byref(s), ctypes.byref(st), key_bits,
                                _ptr(lut), levels, int(threshold), radius, seed & 0xFFFFFFFF,
                                _ptr(xs), _ptr(ys), len(xs), _ptr(out))
+    return out
+
+
+def lookup_only(tgt_guide, src_guide, style, key_bits, lut=None):
+    """Texture-mapping comparator (§4): C_T[p] = C_S[LUT(G_T[p])]."""
+    t, kt = _guide(tgt_guide)
+    s, ks = _guide(src_guide)
+    st, kst = _style(style)
+    if lut is None:
+        lut = new_lut(s.channels, key_bits)
+    out = np.empty((t.height, t.width, 4), dtype=np.uint8)
+    _load().orc_lookup_only(ctypes.byref(t), ctypes.byref(s), ctypes.byref(st), key_bits,
+                            _ptr(lut), _ptr(out))
     return out

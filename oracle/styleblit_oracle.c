@@ -398,3 +398,25 @@ int orc_stylize_points(const orc_guide *tgt, const orc_guide *src, const orc_rgb
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* lookup-only comparator (Section 4: texture mapping / The Lit Sphere)       */
+/* ------------------------------------------------------------------------ */
+
+/* Each target pixel copies the style at the table entry of its own guide
+ * value, C_T[p] = C_S[LUT(G_T[p])]: the per-pixel mapping the paper compares
+ * its chunk transfer against.  No seeds, levels or vote. */
+int orc_lookup_only(const orc_guide *tgt, const orc_guide *src, const orc_rgba8 *style,
+                    int32_t key_bits, uint32_t *lut, uint8_t *out)
+{
+    for (int32_t y = 0; y < tgt->height; ++y) {
+        for (int32_t x = 0; x < tgt->width; ++x) {
+            uint32_t u = lut_lookup(lut, src, key_bits, orc_lut_index(tgt, x, y, key_bits));
+            const uint8_t *c = style->data + (int64_t)(u >> 16) * style->row_stride + 4 * (u & 0xFFFFu);
+            uint8_t *o = out + 4 * ((int64_t)y * tgt->width + x);
+            for (int32_t ch = 0; ch < 4; ++ch)
+                o[ch] = c[ch];
+        }
+    }
+    return 0;
+}

@@ -26,7 +26,7 @@ import torch
 from . import _build
 
 __all__ = ["StyleBlitError", "Lut", "build_lut", "assign_chunks", "blend", "stylize",
-           "stylize_batch", "BatchFrame", "stylize_host", "library_path", "load_library",
+           "stylize_batch", "BatchFrame", "lookup_only", "stylize_host", "library_path", "load_library",
            "EXPORTED_SYMBOLS", "version", "MAX_BATCH"]
 
 MAX_BATCH = 128
@@ -36,7 +36,7 @@ _STATUS = {0: "SB_OK", -1: "SB_ERR_INVALID_ARG", -2: "SB_ERR_UNSUPPORTED", -3: "
            -4: "SB_ERR_OOM", -5: "SB_ERR_TIMEOUT"}
 
 EXPORTED_SYMBOLS = ["sb_build_lut", "sb_build_lut_noalloc", "sb_lut_destroy", "sb_lut_info",
-                    "sb_assign_chunks", "sb_blend", "sb_stylize", "sb_stylize_batch",
+                    "sb_assign_chunks", "sb_blend", "sb_stylize", "sb_stylize_batch", "sb_lookup_only",
                     "sb_status_string", "sb_last_error", "sb_version"]
 
 
@@ -98,6 +98,7 @@ def load_library(build_if_missing: bool = True):
             "sb_stylize": (ctypes.c_int, [P(_Guide), P(_Guide), P(_Rgba8), vp, i32, u64, i32,
                                           u32, vp, vp]),
             "sb_stylize_batch": (ctypes.c_int, [P(_Frame), i32, i32, vp]),
+            "sb_lookup_only": (ctypes.c_int, [P(_Guide), P(_Guide), P(_Rgba8), vp, vp, vp]),
             "sb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "sb_last_error": (ctypes.c_char_p, []),
             "sb_version": (i32, []),
@@ -269,6 +270,20 @@ def stylize(tgt_guide, src_guide, style, lut: Lut, levels: int, threshold: int, 
     _check("sb_stylize", lib.sb_stylize(ctypes.byref(t), ctypes.byref(s), ctypes.byref(st),
                                         lut.handle, levels, int(threshold), radius,
                                         seed & 0xFFFFFFFF, out.data_ptr(), _stream(stream)))
+    return out
+
+
+def lookup_only(tgt_guide, src_guide, style, lut: "Lut", out=None, stream=None):
+    """Texture-mapping comparator (Section 4): C_T[p] = C_S[LUT(G_T[p])]."""
+    lib = load_library()
+    t, s = _guide(tgt_guide, "tgt_guide"), _guide(src_guide, "src_guide")
+    st = _style(style)
+    H, W = tgt_guide.shape[:2]
+    if out is None:
+        out = torch.empty((H, W, 4), dtype=torch.uint8, device=tgt_guide.device)
+    _check("sb_lookup_only", lib.sb_lookup_only(ctypes.byref(t), ctypes.byref(s),
+                                                ctypes.byref(st), lut.handle, out.data_ptr(),
+                                                _stream(stream)))
     return out
 
 

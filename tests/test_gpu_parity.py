@@ -224,3 +224,31 @@ def test_full_size_sampled_parity_and_properties(cuda_device, name):
     d = ((ex.guide[Ay, Ax].astype(np.int64) - fr.guide.astype(np.int64)) ** 2).sum(-1)
     assert (d[lev > 1] <= w.threshold).all()
     assert lev.min() >= 1 and lev.max() <= w.levels
+
+
+# ---------------------------------------------------------------------------
+# lookup-only comparator (Section 4: texture mapping)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["u8x3-48x40-L3-T12000-r1", "u16x2-40x36-L5-T4096-r3",
+                                  "u8x1-31x17-L2-T10-r0"])
+def test_lookup_only_matches_oracle(cuda_device, case):
+    c = make_case(case)
+    gt, gs, st = to_dev(c["tgt"], cuda_device), to_dev(c["src"], cuda_device), to_dev(c["style"], cuda_device)
+    lut = sb.build_lut(gs, c["key_bits"])
+    out = sb.lookup_only(gt, gs, st, lut)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(),
+                          oracle.lookup_only(c["tgt"], c["src"], c["style"], c["key_bits"]))
+
+
+def test_lookup_only_full_size_sampled(cuda_device):
+    w = workload("4k")
+    ex, fr = w.exemplar, w.frames[0]
+    gs, st = to_dev(ex.guide, cuda_device), to_dev(ex.style, cuda_device)
+    lut = sb.build_lut(gs, ex.lut_bits)
+    out = sb.lookup_only(to_dev(fr.guide, cuda_device), gs, st, lut).cpu().numpy()
+    xs, ys = sample_pixels(3, 3840, 2160, 100)
+    for x, y in zip(xs, ys):
+        e = oracle.lut_entry(ex.guide, ex.lut_bits, oracle.lut_index(fr.guide, int(x), int(y), ex.lut_bits))
+        assert (out[y, x] == ex.style[e >> 16, e & 0xFFFF]).all()

@@ -116,3 +116,20 @@ def test_full_build_equals_entries_and_lazy_fill():
     assert np.array_equal(a1, a2) and np.array_equal(l1, l2)
     filled = lazy != oracle.UNSET
     assert filled.any() and np.array_equal(lazy[filled], full[filled])
+
+
+def test_lookup_only_closed_forms():
+    """The texture-mapping comparator: identical identity-UV guides with one
+    guide value per bin return the exemplar itself; a constant target guide
+    returns one constant colour, the style at that value's table entry."""
+    H, W = 24, 40
+    G = synth.identity_uv_guide(H, W)
+    style = synth.random_style(2, H, W)
+    assert np.array_equal(oracle.lookup_only(G, G, style, 11), style)
+    src = synth.random_guide(3, 20, 30, 3)
+    st = synth.random_style(4, 20, 30)
+    tgt = np.empty((7, 9, 3), np.uint8)
+    tgt[...] = [10, 200, 77]
+    out = oracle.lookup_only(tgt, src, st, 5)
+    e = oracle.lut_entry(src, 5, oracle.lut_index(tgt, 0, 0, 5))
+    assert (out == st[e >> 16, e & 0xFFFF]).all()
