@@ -72,18 +72,22 @@ def _load():
                 "orc_lut_index": (u32, [P(_Guide), i32, i32, i32]),
                 "orc_bin_representative": (None, [u32, i32, i32, i32, P(u32)]),
                 "orc_lut_entry": (u32, [P(_Guide), i32, u32]),
-                "orc_build_lut": (ctypes.c_int, [P(_Guide), i32, vp, i32]),
+                "orc_lut_entry_k": (u32, [P(_Guide), i32, i32, u32]),
+                "orc_lut_index_k": (u32, [P(_Guide), i32, i32, i32, i32]),
+                "orc_build_lut": (ctypes.c_int, [P(_Guide), i32, i32, vp, i32]),
                 "orc_seed_point": (None, [i64, i64, i32, u32, i32, i32, P(i64), P(i64)]),
                 "orc_nearest_seed": (None, [i32, i32, i32, u32, i32, i32, P(i32), P(i32)]),
-                "orc_assign": (ctypes.c_int, [P(_Guide), P(_Guide), i32, vp, i32, u64, u32,
-                                              vp, vp, i32]),
-                "orc_assign_points": (ctypes.c_int, [P(_Guide), P(_Guide), i32, vp, i32, u64,
-                                                     u32, vp, vp, i64, vp, vp]),
+                "orc_assign": (ctypes.c_int, [P(_Guide), P(_Guide), i32, i32, vp, i32, u64,
+                                              u32, vp, vp, i32]),
+                "orc_assign_points": (ctypes.c_int, [P(_Guide), P(_Guide), i32, i32, vp, i32,
+                                                     u64, u32, vp, vp, i64, vp, vp]),
                 "orc_blend_rgba8": (ctypes.c_int, [vp, i32, i32, P(_Rgba8), i32, vp, i32]),
                 "orc_blend_f32": (ctypes.c_int, [vp, i32, i32, P(_Rgba8), i32, vp, i32]),
-                "orc_stylize_points": (ctypes.c_int, [P(_Guide), P(_Guide), P(_Rgba8), i32, vp,
-                                                      i32, u64, i32, u32, vp, vp, i64, vp]),
-                "orc_lookup_only": (ctypes.c_int, [P(_Guide), P(_Guide), P(_Rgba8), i32, vp, vp]),
+                "orc_stylize_points": (ctypes.c_int, [P(_Guide), P(_Guide), P(_Rgba8), i32, i32,
+                                                      vp, i32, u64, i32, u32, vp, vp, i64,
+                                                      vp]),
+                "orc_lookup_only": (ctypes.c_int, [P(_Guide), P(_Guide), P(_Rgba8), i32, i32, vp,
+                                                   vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -158,9 +162,10 @@ def new_lut(channels: int, key_bits: int) -> np.ndarray:
     return np.full(lut_size(channels, key_bits), UNSET, dtype=np.uint32)
 
 
-def lut_index(guide: np.ndarray, x: int, y: int, key_bits: int) -> int:
+def lut_index(guide: np.ndarray, x: int, y: int, key_bits: int, key_channels=None) -> int:
     g, keep = _guide(guide)
-    return int(_load().orc_lut_index(ctypes.byref(g), x, y, key_bits))
+    kc = g.channels if key_channels is None else key_channels
+    return int(_load().orc_lut_index_k(ctypes.byref(g), x, y, key_bits, kc))
 
 
 def bin_representative(idx: int, channels: int, bits: int, key_bits: int) -> list[int]:
@@ -169,22 +174,26 @@ def bin_representative(idx: int, channels: int, bits: int, key_bits: int) -> lis
     return [int(rep[c]) for c in range(channels)]
 
 
-def lut_entry(src_guide: np.ndarray, key_bits: int, idx: int) -> int:
+def lut_entry(src_guide: np.ndarray, key_bits: int, idx: int, key_channels=None) -> int:
     g, keep = _guide(src_guide)
-    return int(_load().orc_lut_entry(ctypes.byref(g), key_bits, idx))
+    kc = g.channels if key_channels is None else key_channels
+    return int(_load().orc_lut_entry_k(ctypes.byref(g), key_bits, kc, idx))
 
 
-def lut_entries(src_guide: np.ndarray, key_bits: int, idxs) -> np.ndarray:
+def lut_entries(src_guide: np.ndarray, key_bits: int, idxs, key_channels=None) -> np.ndarray:
     g, keep = _guide(src_guide)
+    kc = g.channels if key_channels is None else key_channels
     lib = _load()
-    return np.array([lib.orc_lut_entry(ctypes.byref(g), key_bits, int(i)) for i in idxs],
+    return np.array([lib.orc_lut_entry_k(ctypes.byref(g), key_bits, kc, int(i)) for i in idxs],
                     dtype=np.uint32)
 
 
-def build_lut(src_guide: np.ndarray, key_bits: int, n_threads: int = 0) -> np.ndarray:
+def build_lut(src_guide: np.ndarray, key_bits: int, n_threads: int = 0,
+              key_channels=None) -> np.ndarray:
     g, keep = _guide(src_guide)
-    lut = np.empty(lut_size(g.channels, key_bits), dtype=np.uint32)
-    _load().orc_build_lut(ctypes.byref(g), key_bits, _ptr(lut), n_threads or os.cpu_count())
+    kc = g.channels if key_channels is None else key_channels
+    lut = np.empty(lut_size(kc, key_bits), dtype=np.uint32)
+    _load().orc_build_lut(ctypes.byref(g), key_bits, kc, _ptr(lut), n_threads or os.cpu_count())
     return lut
 
 
@@ -192,29 +201,33 @@ def build_lut(src_guide: np.ndarray, key_bits: int, n_threads: int = 0) -> np.nd
 # Algorithm 2 level loop and the vote of §3.2
 # --------------------------------------------------------------------------
 
-def assign(tgt_guide, src_guide, key_bits, levels, threshold, seed, lut=None, n_threads=1):
+def assign(tgt_guide, src_guide, key_bits, levels, threshold, seed, lut=None, n_threads=1,
+           key_channels=None):
     """Chunk assignment of every target pixel: (A packed x|y<<16, level)."""
     t, kt = _guide(tgt_guide)
     s, ks = _guide(src_guide)
+    kc = s.channels if key_channels is None else key_channels
     if lut is None:
-        lut = new_lut(s.channels, key_bits)
+        lut = new_lut(kc, key_bits)
     a = np.empty((t.height, t.width), dtype=np.uint32)
     lev = np.empty((t.height, t.width), dtype=np.uint8)
-    _load().orc_assign(ctypes.byref(t), ctypes.byref(s), key_bits, _ptr(lut), levels,
+    _load().orc_assign(ctypes.byref(t), ctypes.byref(s), key_bits, kc, _ptr(lut), levels,
                        int(threshold), seed & 0xFFFFFFFF, _ptr(a), _ptr(lev), n_threads)
     return a, lev
 
 
-def assign_points(tgt_guide, src_guide, key_bits, levels, threshold, seed, xs, ys, lut=None):
+def assign_points(tgt_guide, src_guide, key_bits, levels, threshold, seed, xs, ys, lut=None,
+                  key_channels=None):
     t, kt = _guide(tgt_guide)
     s, ks = _guide(src_guide)
+    kc = s.channels if key_channels is None else key_channels
     if lut is None:
-        lut = new_lut(s.channels, key_bits)
+        lut = new_lut(kc, key_bits)
     xs = np.ascontiguousarray(xs, dtype=np.int32)
     ys = np.ascontiguousarray(ys, dtype=np.int32)
     a = np.empty(len(xs), dtype=np.uint32)
     lev = np.empty(len(xs), dtype=np.uint8)
-    _load().orc_assign_points(ctypes.byref(t), ctypes.byref(s), key_bits, _ptr(lut), levels,
+    _load().orc_assign_points(ctypes.byref(t), ctypes.byref(s), key_bits, kc, _ptr(lut), levels,
                               int(threshold), seed & 0xFFFFFFFF, _ptr(xs), _ptr(ys), len(xs),
                               _ptr(a), _ptr(lev))
     return a, lev
@@ -240,37 +253,40 @@ def blend_f32(assign_map, style, radius, n_threads=1):
 
 
 def stylize(tgt_guide, src_guide, style, key_bits, levels, threshold, radius, seed,
-            lut=None, n_threads=1):
+            lut=None, n_threads=1, key_channels=None):
     """Full frame: assignment, then the RGBA8 vote."""
-    a, lev = assign(tgt_guide, src_guide, key_bits, levels, threshold, seed, lut, n_threads)
+    a, lev = assign(tgt_guide, src_guide, key_bits, levels, threshold, seed, lut, n_threads,
+                    key_channels)
     return blend_rgba8(a, style, radius, n_threads), a, lev
 
 
 def stylize_points(tgt_guide, src_guide, style, key_bits, levels, threshold, radius, seed,
-                   xs, ys, lut=None):
+                   xs, ys, lut=None, key_channels=None):
     """RGBA8 output at selected pixels, each computed from scratch."""
     t, kt = _guide(tgt_guide)
     s, ks = _guide(src_guide)
     st, kst = _style(style)
+    kc = s.channels if key_channels is None else key_channels
     if lut is None:
-        lut = new_lut(s.channels, key_bits)
+        lut = new_lut(kc, key_bits)
     xs = np.ascontiguousarray(xs, dtype=np.int32)
     ys = np.ascontiguousarray(ys, dtype=np.int32)
     out = np.empty((len(xs), 4), dtype=np.uint8)
     _load().orc_stylize_points(ctypes.byref(t), ctypes.byref(s), ctypes.byref(st), key_bits,
-                               _ptr(lut), levels, int(threshold), radius, seed & 0xFFFFFFFF,
+                               kc, _ptr(lut), levels, int(threshold), radius, seed & 0xFFFFFFFF,
                                _ptr(xs), _ptr(ys), len(xs), _ptr(out))
     return out
 
 
-def lookup_only(tgt_guide, src_guide, style, key_bits, lut=None):
+def lookup_only(tgt_guide, src_guide, style, key_bits, lut=None, key_channels=None):
     """Texture-mapping comparator (§4): C_T[p] = C_S[LUT(G_T[p])]."""
     t, kt = _guide(tgt_guide)
     s, ks = _guide(src_guide)
     st, kst = _style(style)
+    kc = s.channels if key_channels is None else key_channels
     if lut is None:
-        lut = new_lut(s.channels, key_bits)
+        lut = new_lut(kc, key_bits)
     out = np.empty((t.height, t.width, 4), dtype=np.uint8)
-    _load().orc_lookup_only(ctypes.byref(t), ctypes.byref(s), ctypes.byref(st), key_bits,
+    _load().orc_lookup_only(ctypes.byref(t), ctypes.byref(s), ctypes.byref(st), key_bits, kc,
                             _ptr(lut), _ptr(out))
     return out

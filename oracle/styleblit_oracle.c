@@ -49,6 +49,11 @@
  *       (integer division, round half up); alpha is voted like colour.  The
  *       float variant returns sum / (255 n).
  *   R10 every pixel compares single pixels (Algorithm 2), not regions.
+ *   R11 extra guide channels (Section 4 adds a segmentation guide to keep
+ *       chunks inside semantic regions): the table is keyed on the first
+ *       key_channels channels (the local guide) and maps a bin to the source
+ *       pixel nearest in those channels; the acceptance distance (R1) uses
+ *       every channel.
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -101,13 +106,23 @@ static uint64_t guide_distance(const orc_guide *a, int64_t ax, int64_t ay,
 /* look-up table (Section 3.1; reading R8)                                    */
 /* ------------------------------------------------------------------------ */
 
-uint32_t orc_lut_index(const orc_guide *g, int32_t x, int32_t y, int32_t key_bits)
+/* Table index of pixel (x, y): the top key_bits bits of each of the first
+ * key_channels channels (the local guide; further channels, e.g. a
+ * segmentation channel of Section 4, take part only in the acceptance
+ * distance), concatenated with channel 0 lowest. */
+uint32_t orc_lut_index_k(const orc_guide *g, int32_t x, int32_t y, int32_t key_bits,
+                         int32_t key_channels)
 {
     int32_t shift = g->bits - key_bits;
     uint32_t idx = 0;
-    for (int32_t c = 0; c < g->channels; ++c)
+    for (int32_t c = 0; c < key_channels; ++c)
         idx |= (guide_value(g, x, y, c) >> shift) << (c * key_bits);
     return idx;
+}
+
+uint32_t orc_lut_index(const orc_guide *g, int32_t x, int32_t y, int32_t key_bits)
+{
+    return orc_lut_index_k(g, x, y, key_bits, g->channels);
 }
 
 void orc_bin_representative(uint32_t idx, int32_t channels, int32_t bits,
@@ -124,16 +139,17 @@ void orc_bin_representative(uint32_t idx, int32_t channels, int32_t bits,
 /* One table entry by its definition: the source pixel whose guide is nearest
  * to the bin representative, scanning in raster order and keeping the first
  * minimum, which is the smallest linear index among ties. */
-uint32_t orc_lut_entry(const orc_guide *src, int32_t key_bits, uint32_t idx)
+uint32_t orc_lut_entry_k(const orc_guide *src, int32_t key_bits, int32_t key_channels,
+                         uint32_t idx)
 {
     uint32_t rep[4];
-    orc_bin_representative(idx, src->channels, src->bits, key_bits, rep);
+    orc_bin_representative(idx, key_channels, src->bits, key_bits, rep);
     uint64_t best = UINT64_MAX;
     uint32_t best_xy = 0;
     for (int32_t y = 0; y < src->height; ++y) {
         for (int32_t x = 0; x < src->width; ++x) {
             uint64_t d = 0;
-            for (int32_t c = 0; c < src->channels; ++c) {
+            for (int32_t c = 0; c < key_channels; ++c) {
                 int64_t diff = (int64_t)rep[c] - (int64_t)guide_value(src, x, y, c);
                 d += (uint64_t)(diff * diff);
             }
@@ -146,25 +162,32 @@ uint32_t orc_lut_entry(const orc_guide *src, int32_t key_bits, uint32_t idx)
     return best_xy;
 }
 
+uint32_t orc_lut_entry(const orc_guide *src, int32_t key_bits, uint32_t idx)
+{
+    return orc_lut_entry_k(src, key_bits, src->channels, idx);
+}
+
 /* A table entry, computed on first use.  Unfilled entries hold ORC_UNSET (no
  * valid entry has x = y = 65535 since source sides are at most 65535). */
-static uint32_t lut_lookup(uint32_t *lut, const orc_guide *src, int32_t key_bits, uint32_t idx)
+static uint32_t lut_lookup(uint32_t *lut, const orc_guide *src, int32_t key_bits,
+                           int32_t key_channels, uint32_t idx)
 {
     uint32_t v = __atomic_load_n(&lut[idx], __ATOMIC_RELAXED);
     if (v == ORC_UNSET) {
-        v = orc_lut_entry(src, key_bits, idx);
+        v = orc_lut_entry_k(src, key_bits, key_channels, idx);
         __atomic_store_n(&lut[idx], v, __ATOMIC_RELAXED);
     }
     return v;
 }
 
-int orc_build_lut(const orc_guide *src, int32_t key_bits, uint32_t *lut, int32_t n_threads)
+int orc_build_lut(const orc_guide *src, int32_t key_bits, int32_t key_channels, uint32_t *lut,
+                  int32_t n_threads)
 {
-    int64_t n = (int64_t)1 << (src->channels * key_bits);
+    int64_t n = (int64_t)1 << (key_channels * key_bits);
     (void)n_threads;
 #pragma omp parallel for schedule(dynamic, 64) num_threads(n_threads > 0 ? n_threads : 1)
     for (int64_t i = 0; i < n; ++i)
-        lut[i] = orc_lut_entry(src, key_bits, (uint32_t)i);
+        lut[i] = orc_lut_entry_k(src, key_bits, key_channels, (uint32_t)i);
     return 0;
 }
 
@@ -245,13 +268,15 @@ void orc_nearest_seed(int32_t px, int32_t py, int32_t level, uint32_t seed,
  * candidate u* + (p - q) and accept it when its guide distance to G_T[p] is
  * within the threshold (R1, R7); the finest level always accepts (R2). */
 static void assign_pixel(const orc_guide *tgt, const orc_guide *src, int32_t key_bits,
-                         uint32_t *lut, int32_t levels, uint64_t threshold, uint32_t seed,
-                         int32_t px, int32_t py, uint32_t *a_out, uint8_t *level_out)
+                         int32_t key_channels, uint32_t *lut, int32_t levels,
+                         uint64_t threshold, uint32_t seed, int32_t px, int32_t py,
+                         uint32_t *a_out, uint8_t *level_out)
 {
     for (int32_t l = levels; l >= 1; --l) {
         int32_t qx, qy;
         orc_nearest_seed(px, py, l, seed, tgt->width, tgt->height, &qx, &qy);
-        uint32_t u = lut_lookup(lut, src, key_bits, orc_lut_index(tgt, qx, qy, key_bits));
+        uint32_t u = lut_lookup(lut, src, key_bits, key_channels,
+                                orc_lut_index_k(tgt, qx, qy, key_bits, key_channels));
         int64_t sx = (int64_t)(u & 0xFFFFu) + ((int64_t)px - qx);
         int64_t sy = (int64_t)(u >> 16) + ((int64_t)py - qy);
         if (l > 1) {
@@ -269,9 +294,9 @@ static void assign_pixel(const orc_guide *tgt, const orc_guide *src, int32_t key
     }
 }
 
-int orc_assign(const orc_guide *tgt, const orc_guide *src, int32_t key_bits, uint32_t *lut,
-               int32_t levels, uint64_t threshold, uint32_t seed,
-               uint32_t *assign, uint8_t *level, int32_t n_threads)
+int orc_assign(const orc_guide *tgt, const orc_guide *src, int32_t key_bits,
+               int32_t key_channels, uint32_t *lut, int32_t levels, uint64_t threshold,
+               uint32_t seed, uint32_t *assign, uint8_t *level, int32_t n_threads)
 {
     (void)n_threads;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : 1)
@@ -279,7 +304,7 @@ int orc_assign(const orc_guide *tgt, const orc_guide *src, int32_t key_bits, uin
         for (int32_t x = 0; x < tgt->width; ++x) {
             int64_t i = (int64_t)y * tgt->width + x;
             uint8_t l;
-            assign_pixel(tgt, src, key_bits, lut, levels, threshold, seed, x, y,
+            assign_pixel(tgt, src, key_bits, key_channels, lut, levels, threshold, seed, x, y,
                          &assign[i], &l);
             if (level)
                 level[i] = l;
@@ -289,13 +314,13 @@ int orc_assign(const orc_guide *tgt, const orc_guide *src, int32_t key_bits, uin
 }
 
 int orc_assign_points(const orc_guide *tgt, const orc_guide *src, int32_t key_bits,
-                      uint32_t *lut, int32_t levels, uint64_t threshold, uint32_t seed,
-                      const int32_t *xs, const int32_t *ys, int64_t n,
-                      uint32_t *assign, uint8_t *level)
+                      int32_t key_channels, uint32_t *lut, int32_t levels,
+                      uint64_t threshold, uint32_t seed, const int32_t *xs, const int32_t *ys,
+                      int64_t n, uint32_t *assign, uint8_t *level)
 {
     for (int64_t i = 0; i < n; ++i)
-        assign_pixel(tgt, src, key_bits, lut, levels, threshold, seed, xs[i], ys[i],
-                     &assign[i], &level[i]);
+        assign_pixel(tgt, src, key_bits, key_channels, lut, levels, threshold, seed, xs[i],
+                     ys[i], &assign[i], &level[i]);
     return 0;
 }
 
@@ -367,7 +392,8 @@ int orc_blend_f32(const uint32_t *assign, int32_t tgt_w, int32_t tgt_h,
  * neighbour's assignment from scratch: slow, but needs no full-frame buffer,
  * so it can check sampled pixels of frames of any size. */
 int orc_stylize_points(const orc_guide *tgt, const orc_guide *src, const orc_rgba8 *style,
-                       int32_t key_bits, uint32_t *lut, int32_t levels, uint64_t threshold,
+                       int32_t key_bits, int32_t key_channels, uint32_t *lut, int32_t levels,
+                       uint64_t threshold,
                        int32_t radius, uint32_t seed, const int32_t *xs, const int32_t *ys,
                        int64_t n, uint8_t *out)
 {
@@ -381,7 +407,7 @@ int orc_stylize_points(const orc_guide *tgt, const orc_guide *src, const orc_rgb
                     continue;
                 uint32_t a;
                 uint8_t l;
-                assign_pixel(tgt, src, key_bits, lut, levels, threshold, seed,
+                assign_pixel(tgt, src, key_bits, key_channels, lut, levels, threshold, seed,
                              (int32_t)nx, (int32_t)ny, &a, &l);
                 int64_t vx = (int64_t)(a & 0xFFFFu) - ox;
                 int64_t vy = (int64_t)(a >> 16) - oy;
@@ -407,11 +433,12 @@ int orc_stylize_points(const orc_guide *tgt, const orc_guide *src, const orc_rgb
  * value, C_T[p] = C_S[LUT(G_T[p])]: the per-pixel mapping the paper compares
  * its chunk transfer against.  No seeds, levels or vote. */
 int orc_lookup_only(const orc_guide *tgt, const orc_guide *src, const orc_rgba8 *style,
-                    int32_t key_bits, uint32_t *lut, uint8_t *out)
+                    int32_t key_bits, int32_t key_channels, uint32_t *lut, uint8_t *out)
 {
     for (int32_t y = 0; y < tgt->height; ++y) {
         for (int32_t x = 0; x < tgt->width; ++x) {
-            uint32_t u = lut_lookup(lut, src, key_bits, orc_lut_index(tgt, x, y, key_bits));
+            uint32_t u = lut_lookup(lut, src, key_bits, key_channels,
+                                    orc_lut_index_k(tgt, x, y, key_bits, key_channels));
             const uint8_t *c = style->data + (int64_t)(u >> 16) * style->row_stride + 4 * (u & 0xFFFFu);
             uint8_t *o = out + 4 * ((int64_t)y * tgt->width + x);
             for (int32_t ch = 0; ch < 4; ++ch)

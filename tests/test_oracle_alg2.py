@@ -53,8 +53,10 @@ def _nearest_seed(p, h, level, seed, W, H):
     return s_best
 
 
-def _parallel_styleblit(GT, GS, T, L, seed):
-    """Algorithm 2 per pixel, u* by brute-force argmin over all source pixels."""
+def _parallel_styleblit(GT, GS, T, L, seed, key_channels=None):
+    """Algorithm 2 per pixel, u* by brute-force argmin over all source pixels
+    (over the first key_channels channels; the acceptance uses all)."""
+    kc = GS.shape[2] if key_channels is None else key_channels
     Ht, Wt = GT.shape[:2]
     Hs, Ws = GS.shape[:2]
     gs = GS.reshape(-1, GS.shape[2]).astype(np.int64)
@@ -65,7 +67,7 @@ def _parallel_styleblit(GT, GS, T, L, seed):
             for level in range(L, 0, -1):
                 h = 2 ** level
                 q = _nearest_seed((px, py), h, level, seed, Wt, Ht)
-                d = ((gs - GT[q[1], q[0]].astype(np.int64)) ** 2).sum(axis=1)
+                d = ((gs[:, :kc] - GT[q[1], q[0], :kc].astype(np.int64)) ** 2).sum(axis=1)
                 u_lin = int(np.argmin(d))  # first minimum = smallest linear index
                 u = (u_lin % Ws, u_lin // Ws)
                 s = (u[0] + px - q[0], u[1] + py - q[1])
@@ -209,3 +211,25 @@ def test_points_api_matches_full_frame():
     po = oracle.stylize_points(fr.guide, ex.guide, ex.style, ex.lut_bits, w.levels,
                                w.threshold, 2, w.seed, xs, ys)
     assert np.array_equal(po, out[ys, xs])
+
+
+@pytest.mark.parametrize("T,seed", [(100, 3), (900, 11)])
+def test_segmentation_channel_keys_and_acceptance(T, seed):
+    """Section 4 adds a segmentation guide: the table is keyed on the local
+    guide only (first two channels here), the acceptance distance includes the
+    segment channel (0 or 255).  Literal transcription agrees, and with
+    T < 255^2 no accepted chunk crosses a segment boundary."""
+    Ht, Wt, Hs, Ws = 22, 26, 16, 18
+    GT = synth.smooth_integer_guide(40 + seed, Ht, Wt, 3, step=4)
+    GS = synth.smooth_integer_guide(50 + seed, Hs, Ws, 3, step=4)
+    GT[..., 2] = np.where(np.arange(Wt)[None, :] < Wt // 2, 0, 255)
+    GS[..., 2] = np.where(np.arange(Hs)[:, None] < Hs // 3, 255, 0)
+    A_ref, lev_ref = _parallel_styleblit(GT, GS, T, 4, seed, key_channels=2)
+    a, lev = oracle.assign(GT, GS, 8, 4, T, seed, key_channels=2)
+    assert np.array_equal(_unpack(a), A_ref) and np.array_equal(lev.astype(np.int64), lev_ref)
+    A = _unpack(a)
+    seg_src = GS[A[..., 1], A[..., 0], 2]
+    assert (seg_src[lev > 1] == GT[..., 2][lev > 1]).all()
+    # keying on every channel gives a different (larger) table and, here, a different result
+    a_all, _ = oracle.assign(GT, GS, 8, 4, T, seed)
+    assert not np.array_equal(a_all, a)

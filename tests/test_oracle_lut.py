@@ -133,3 +133,20 @@ def test_lookup_only_closed_forms():
     out = oracle.lookup_only(tgt, src, st, 5)
     e = oracle.lut_entry(src, 5, oracle.lut_index(tgt, 0, 0, 5))
     assert (out == st[e >> 16, e & 0xFFFF]).all()
+
+
+def test_key_channels_subset_matches_kdtree_on_those_channels():
+    """A table keyed on the first key_channels channels maps a bin to the pixel
+    nearest in those channels only (the rest are for acceptance)."""
+    spatial = pytest.importorskip("scipy.spatial")
+    src = synth.random_guide(77, 20, 25, 4, bits=8)
+    kc, kb = 2, 6
+    idxs = np.arange(1 << (kc * kb))
+    got = oracle.lut_entries(src, kb, idxs, key_channels=kc)
+    reps = np.array([oracle.bin_representative(int(i), kc, 8, kb) for i in idxs], np.int64)
+    dist, _ = spatial.cKDTree(src[..., :kc].reshape(-1, kc).astype(np.float64)).query(reps)
+    chosen = src[got >> 16, got & 0xFFFF, :kc].astype(np.int64)
+    assert np.array_equal(((chosen - reps) ** 2).sum(1), np.rint(dist ** 2).astype(np.int64))
+    assert oracle.lut_index(src, 3, 4, kb, key_channels=kc) < (1 << (kc * kb))
+    full = oracle.build_lut(src, kb, key_channels=kc)
+    assert np.array_equal(full, got)
