@@ -145,13 +145,29 @@ SB_API sb_status sb_build_lut_noalloc(const sb_guide *src_guide, int32_t key_bit
  * still uses it (e.g. synchronise the streams that used it first). */
 SB_API sb_status sb_lut_destroy(sb_lut *lut);
 
-/* Describes a table: device pointer to its 2^(channels*key_bits) uint32
- * entries (packed x | y << 16), entry count, channels, bits and key_bits of
- * the guide it was built for, and that guide's width and height.  Any output
- * pointer may be NULL. */
+/* Describes a table: device pointer to its 2^(key_channels*key_bits) uint32
+ * entries (packed x | y << 16), entry count, channels and bits of the guide
+ * it was built for, key_bits, key_channels, and that guide's width and height.
+ * Any output pointer may be NULL. */
 SB_API sb_status sb_lut_info(const sb_lut *lut, const uint32_t **entries, int64_t *n_entries,
-                      int32_t *channels, int32_t *bits, int32_t *key_bits,
-                      int32_t *src_width, int32_t *src_height);
+                             int32_t *channels, int32_t *bits, int32_t *key_bits,
+                             int32_t *key_channels, int32_t *src_width, int32_t *src_height);
+
+/*
+ * sb_build_lut_keyed -- sb_build_lut keyed on the first key_channels guide
+ * channels only.  Section 4 adds a segmentation guide that keeps chunks inside
+ * semantic regions: such channels are appended after the local guide (e.g.
+ * uint8 normals + one segment channel = 4 channels) and take part only in the
+ * acceptance distance of sb_assign_chunks / sb_stylize / sb_stylize_batch,
+ * while the table maps the local guide to the source pixel nearest in those
+ * key channels (ties to the smallest y * width + x).
+ *
+ *   key_channels  1..channels; key_channels * key_bits <= 24.
+ *   Other arguments, ownership and errors as sb_build_lut (which is this call
+ *   with key_channels = channels).
+ */
+SB_API sb_status sb_build_lut_keyed(const sb_guide *src_guide, int32_t key_bits,
+                                    int32_t key_channels, sb_lut **out, sb_stream stream);
 
 /*
  * sb_assign_chunks -- Algorithm 2 (ParallelStyleBlit) with coordinate

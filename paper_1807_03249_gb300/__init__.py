@@ -35,7 +35,7 @@ SB_OK = 0
 _STATUS = {0: "SB_OK", -1: "SB_ERR_INVALID_ARG", -2: "SB_ERR_UNSUPPORTED", -3: "SB_ERR_CUDA",
            -4: "SB_ERR_OOM", -5: "SB_ERR_TIMEOUT"}
 
-EXPORTED_SYMBOLS = ["sb_build_lut", "sb_build_lut_noalloc", "sb_lut_destroy", "sb_lut_info",
+EXPORTED_SYMBOLS = ["sb_build_lut", "sb_build_lut_keyed", "sb_build_lut_noalloc", "sb_lut_destroy", "sb_lut_info",
                     "sb_assign_chunks", "sb_blend", "sb_stylize", "sb_stylize_batch", "sb_lookup_only",
                     "sb_status_string", "sb_last_error", "sb_version"]
 
@@ -89,9 +89,10 @@ def load_library(build_if_missing: bool = True):
         sigs = {
             "sb_build_lut": (ctypes.c_int, [P(_Guide), i32, P(vp), vp]),
             "sb_build_lut_noalloc": (ctypes.c_int, [P(_Guide), i32, vp, vp]),
+            "sb_build_lut_keyed": (ctypes.c_int, [P(_Guide), i32, i32, P(vp), vp]),
             "sb_lut_destroy": (ctypes.c_int, [vp]),
             "sb_lut_info": (ctypes.c_int, [vp, P(vp), P(i64), P(i32), P(i32), P(i32), P(i32),
-                                           P(i32)]),
+                                           P(i32), P(i32)]),
             "sb_assign_chunks": (ctypes.c_int, [P(_Guide), P(_Guide), vp, i32, u64, u32, vp, vp,
                                                 vp]),
             "sb_blend": (ctypes.c_int, [vp, i32, i32, P(_Rgba8), i32, vp, vp, vp]),
@@ -186,12 +187,13 @@ class Lut:
     def info(self) -> dict:
         e = ctypes.c_void_p()
         n = ctypes.c_int64()
-        c, b, k, w, h = (ctypes.c_int32() for _ in range(5))
+        c, b, k, kc, w, h = (ctypes.c_int32() for _ in range(6))
         _check("sb_lut_info", load_library().sb_lut_info(
             self.handle, ctypes.byref(e), ctypes.byref(n), ctypes.byref(c), ctypes.byref(b),
-            ctypes.byref(k), ctypes.byref(w), ctypes.byref(h)))
+            ctypes.byref(k), ctypes.byref(kc), ctypes.byref(w), ctypes.byref(h)))
         return dict(entries_ptr=e.value, n_entries=n.value, channels=c.value, bits=b.value,
-                    key_bits=k.value, src_width=w.value, src_height=h.value)
+                    key_bits=k.value, key_channels=kc.value, src_width=w.value,
+                    src_height=h.value)
 
     def entries(self) -> torch.Tensor:
         """A copy of the table (int32 bit patterns of x | y << 16), ordered on
@@ -215,12 +217,15 @@ class Lut:
             pass
 
 
-def build_lut(src_guide: torch.Tensor, key_bits: int, stream=None) -> Lut:
+def build_lut(src_guide: torch.Tensor, key_bits: int, stream=None, key_channels=None) -> Lut:
+    """Guide table (Section 3.1) keyed on every channel, or on the first
+    key_channels (extra channels then only enter the acceptance distance)."""
     lib = load_library()
     g = _guide(src_guide, "src_guide")
     h = ctypes.c_void_p()
-    _check("sb_build_lut", lib.sb_build_lut(ctypes.byref(g), key_bits, ctypes.byref(h),
-                                            _stream(stream)))
+    kc = g.channels if key_channels is None else key_channels
+    _check("sb_build_lut_keyed", lib.sb_build_lut_keyed(ctypes.byref(g), key_bits, kc,
+                                                        ctypes.byref(h), _stream(stream)))
     return Lut(h.value, src_guide.shape, src_guide.device)
 
 

@@ -58,6 +58,7 @@ struct FrameArgs {
     int Ws, Hs;
     const uint32_t *lut;
     int key_bits;
+    int key_channels;
     const uint8_t *style;
     int64_t style_stride;
     int levels;
@@ -167,7 +168,7 @@ __device__ __forceinline__ void build_cells(const FrameArgs &a, int4 *cells, int
         const int sx = min(max(bx * h + ox, 0), a.W - 1);
         const int sy = min(max(by * h + oy, 0), a.H - 1);
         const uint32_t u =
-            __ldg(a.lut + F::key(F::load(a.tgt, a.tgt_stride, sx, sy), a.key_bits));
+            __ldg(a.lut + F::key(F::load(a.tgt, a.tgt_stride, sx, sy), a.key_bits, a.key_channels));
         const int qx = sx - cxo, qy = sy - cyo;
         int4 cell;
         if (l <= kPackedMaxLevel) {

@@ -107,6 +107,7 @@ static FrameArgs frame_args(const sb_guide *tgt, const sb_lut *lut, int32_t leve
     a.Hs = lut->src_h;
     a.lut = lut->entries;
     a.key_bits = lut->key_bits;
+    a.key_channels = lut->key_channels;
     a.levels = levels;
     a.threshold = threshold;
     a.seed = seed;

@@ -19,6 +19,7 @@ struct sb_lut {
     int32_t channels = 0;
     int32_t bits = 0;
     int32_t key_bits = 0;
+    int32_t key_channels = 0;      // the table keys the first key_channels guide channels
     int32_t src_w = 0;
     int32_t src_h = 0;
     int32_t device = 0;
@@ -125,13 +126,20 @@ struct GuideFmt {
         }
     }
 
-    // table index: channel keys (top key_bits bits), channel 0 lowest
-    __device__ __forceinline__ static uint32_t key(uint32_t v, int key_bits) {
+    // table index: keys (top key_bits bits) of the first key_channels
+    // channels, channel 0 lowest
+    __device__ __forceinline__ static uint32_t key(uint32_t v, int key_bits, int key_channels) {
         const int z = B - key_bits;
         uint32_t idx = 0;
 #pragma unroll
-        for (int c = 0; c < C; ++c) idx |= (chan(v, c) >> z) << (c * key_bits);
+        for (int c = 0; c < C; ++c)
+            if (c < key_channels) idx |= (chan(v, c) >> z) << (c * key_bits);
         return idx;
+    }
+
+    // v with the channels from key_channels on cleared
+    __device__ __forceinline__ static uint32_t key_part(uint32_t v, int key_channels) {
+        return key_channels * B >= 32 ? v : (v & ((1u << (key_channels * B)) - 1u));
     }
 };
 

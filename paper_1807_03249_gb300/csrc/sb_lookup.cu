@@ -13,14 +13,15 @@ constexpr int kLookupThreads = 256;
 template <int C, int B>
 __global__ void __launch_bounds__(kLookupThreads)
     lookup_kernel(const uint8_t *__restrict__ tgt, int64_t tgt_stride, int W,
-                  const uint32_t *__restrict__ lut, int key_bits,
+                  const uint32_t *__restrict__ lut, int key_bits, int key_channels,
                   const uint32_t *__restrict__ style, int64_t style_stride_px,
                   uint32_t *__restrict__ out) {
     using F = GuideFmt<C, B>;
     const int x = blockIdx.x * kLookupThreads + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= W) return;
-    const uint32_t u = __ldg(lut + F::key(F::load(tgt, tgt_stride, x, y), key_bits));
+    const uint32_t u =
+        __ldg(lut + F::key(F::load(tgt, tgt_stride, x, y), key_bits, key_channels));
     out[(int64_t)y * W + x] = __ldg(style + (int64_t)(u >> 16) * style_stride_px + (u & 0xFFFFu));
 }
 
@@ -35,7 +36,7 @@ struct LookupLaunch {
         const dim3 grid((tgt->width + kLookupThreads - 1) / kLookupThreads, tgt->height);
         lookup_kernel<C, B><<<grid, kLookupThreads, 0, s>>>(
             static_cast<const uint8_t *>(tgt->data), tgt->row_stride, tgt->width, lut->entries,
-            lut->key_bits, reinterpret_cast<const uint32_t *>(style->data), style->row_stride / 4,
+            lut->key_bits, lut->key_channels, reinterpret_cast<const uint32_t *>(style->data), style->row_stride / 4,
             out);
     }
 };

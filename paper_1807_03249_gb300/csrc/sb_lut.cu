@@ -86,11 +86,12 @@ __global__ void __launch_bounds__(256) lut_tile_bounds_kernel(const uint8_t *__r
 
 // squared distance from a representative to a tile's guide box
 template <int C, int B>
-__device__ __forceinline__ uint64_t box_distance(const uint32_t (&rep)[C], uint4 bb) {
+__device__ __forceinline__ uint64_t box_distance(const uint32_t (&rep)[C], uint4 bb, int kc) {
     const uint32_t w[4] = {bb.x, bb.y, bb.z, bb.w};
     uint64_t lb = 0;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
+        if (c >= kc) break;
         const uint32_t lo = w[c] & 0xFFFFu, hi = w[c] >> 16;
         const uint32_t t = rep[c] < lo ? lo - rep[c] : (rep[c] > hi ? rep[c] - hi : 0u);
         lb += (uint64_t)t * t;
@@ -119,7 +120,8 @@ struct RawReader {
 
 template <int C, int B, typename Reader>
 __device__ __forceinline__ void scan_tile(const Reader &rd, int W, int H, int tiles_x, int t,
-                                          uint32_t rep_packed, uint64_t &bd, uint32_t &bl) {
+                                          uint32_t rep_packed, int kc, uint64_t &bd,
+                                          uint32_t &bl) {
     using F = GuideFmt<C, B>;
     const int x0 = (t % tiles_x) * kLutTile;
     const int y0 = (t / tiles_x) * kLutTile;
@@ -127,7 +129,7 @@ __device__ __forceinline__ void scan_tile(const Reader &rd, int W, int H, int ti
     for (int y = y0; y < y1; ++y) {
 #pragma unroll 4
         for (int x = x0; x < x1; ++x) {
-            const uint64_t d = F::dist(rep_packed, rd(x, y));
+            const uint64_t d = F::dist(rep_packed, F::key_part(rd(x, y), kc));
             const uint32_t lin = (uint32_t)y * (uint32_t)W + (uint32_t)x;
             if (d < bd || (d == bd && lin < bl)) {
                 bd = d;
@@ -140,24 +142,26 @@ __device__ __forceinline__ void scan_tile(const Reader &rd, int W, int H, int ti
 template <int C, int B, typename Reader>
 __global__ void __launch_bounds__(kLutThreads)
     lut_search_kernel(const Reader rd, int W, int H, int tiles_x, int n_tiles,
-                      const uint4 *__restrict__ bounds, int key_bits, uint32_t n_bins,
+                      const uint4 *__restrict__ bounds, int key_bits, int kc, uint32_t n_bins,
                       uint32_t *__restrict__ lut) {
     const uint32_t g = blockIdx.x * kLutThreads + threadIdx.x;
     const bool valid = g < n_bins;
 
-    // Morton order: bit b*C + c of g is bit b of channel c's key
+    // Morton order over the kc key channels: bit b*kc + c of g is bit b of
+    // channel c's key; channels from kc on are not keyed
     uint32_t key[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) key[c] = 0;
 #pragma unroll
     for (int c = 0; c < C; ++c)
-        for (int b = 0; b < key_bits; ++b) key[c] |= ((g >> (b * C + c)) & 1u) << b;
+        if (c < kc)
+            for (int b = 0; b < key_bits; ++b) key[c] |= ((g >> (b * kc + c)) & 1u) << b;
     const int z = B - key_bits;
     uint32_t rep[C];
     uint32_t rep_packed = 0, idx = 0;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-        rep[c] = (key[c] << z) + (((1u << z) - 1u) >> 1);
+        rep[c] = c < kc ? (key[c] << z) + (((1u << z) - 1u) >> 1) : 0u;
         rep_packed |= rep[c] << (c * B);
         idx |= key[c] << (c * key_bits);
     }
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(kLutThreads)
     uint64_t best_lb = ~0ull;
     int best_t = 0;
     for (int t = 0; t < n_tiles; ++t) {
-        const uint64_t lb = box_distance<C, B>(rep, __ldg(&bounds[t]));
+        const uint64_t lb = box_distance<C, B>(rep, __ldg(&bounds[t]), kc);
         if (lb < best_lb) {
             best_lb = lb;
             best_t = t;
@@ -175,14 +179,15 @@ __global__ void __launch_bounds__(kLutThreads)
     // pass B: an initial best from that tile
     uint64_t bd = ~0ull;
     uint32_t bl = 0xFFFFFFFFu;
-    scan_tile<C, B>(rd, W, H, tiles_x, best_t, rep_packed, bd, bl);
+    scan_tile<C, B>(rd, W, H, tiles_x, best_t, rep_packed, kc, bd, bl);
     // pass C: every tile that could still hold a better or tied-earlier pixel
     for (int t = 0; t < n_tiles; ++t) {
-        const uint64_t lb = box_distance<C, B>(rep, __ldg(&bounds[t]));
+        const uint64_t lb = box_distance<C, B>(rep, __ldg(&bounds[t]), kc);
         const uint32_t first = (uint32_t)((t / tiles_x) * kLutTile) * (uint32_t)W +
                                (uint32_t)((t % tiles_x) * kLutTile);
         const bool need = valid && (lb < bd || (lb == bd && first < bl));
-        if (__any_sync(0xFFFFFFFFu, need)) scan_tile<C, B>(rd, W, H, tiles_x, t, rep_packed, bd, bl);
+        if (__any_sync(0xFFFFFFFFu, need))
+            scan_tile<C, B>(rd, W, H, tiles_x, t, rep_packed, kc, bd, bl);
     }
     if (valid) lut[idx] = (bl % (uint32_t)W) | ((bl / (uint32_t)W) << 16);
 }
@@ -190,6 +195,7 @@ __global__ void __launch_bounds__(kLutThreads)
 struct LutLaunch {
     const sb_guide *src;
     int key_bits;
+    int key_channels;
     uint32_t n_bins;
     uint4 *bounds;
     uint32_t *entries;
@@ -210,11 +216,11 @@ struct LutLaunch {
                 p, src->row_stride, src->width, src->height, packed);
             lut_search_kernel<C, B><<<search_blocks, kLutThreads, 0, stream>>>(
                 PackedReader{packed, src->width}, src->width, src->height, tiles_x, n_tiles,
-                bounds, key_bits, n_bins, entries);
+                bounds, key_bits, key_channels, n_bins, entries);
         } else {
             lut_search_kernel<C, B><<<search_blocks, kLutThreads, 0, stream>>>(
                 RawReader<C, B>{p, src->row_stride}, src->width, src->height, tiles_x, n_tiles,
-                bounds, key_bits, n_bins, entries);
+                bounds, key_bits, key_channels, n_bins, entries);
         }
     }
 };
@@ -223,25 +229,28 @@ struct LutLaunch {
 
 using namespace sb;
 
-extern "C" sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, sb_lut **out,
-                                  sb_stream stream) {
+extern "C" sb_status sb_build_lut_keyed(const sb_guide *src_guide, int32_t key_bits,
+                                        int32_t key_channels, sb_lut **out, sb_stream stream) {
     sb_status st = check_guide(src_guide, "src_guide", true);
     if (st != SB_OK) return st;
     if (!out) return fail(SB_ERR_INVALID_ARG, "out: NULL");
     if (key_bits < 1 || key_bits > src_guide->bits)
         return fail(SB_ERR_INVALID_ARG, "key_bits must be in [1, bits]");
-    if (src_guide->channels * key_bits > kMaxKeyBitsTotal)
-        return fail(SB_ERR_INVALID_ARG, "channels * key_bits must be <= 24");
+    if (key_channels < 1 || key_channels > src_guide->channels)
+        return fail(SB_ERR_INVALID_ARG, "key_channels must be in [1, channels]");
+    if (key_channels * key_bits > kMaxKeyBitsTotal)
+        return fail(SB_ERR_INVALID_ARG, "key_channels * key_bits must be <= 24");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) return cuda_fail(e, "sb_build_lut: pending CUDA error");
 
-    const uint32_t n_bins = 1u << (src_guide->channels * key_bits);
+    const uint32_t n_bins = 1u << (key_channels * key_bits);
     const int tiles_x = (src_guide->width + kLutTile - 1) / kLutTile;
     const int tiles_y = (src_guide->height + kLutTile - 1) / kLutTile;
     const size_t n_tiles = (size_t)tiles_x * tiles_y;
 
     sb_lut *lut = new sb_lut;
+    lut->key_channels = key_channels;
     lut->n_entries = n_bins;
     lut->channels = src_guide->channels;
     lut->bits = src_guide->bits;
@@ -266,7 +275,8 @@ extern "C" sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, s
         delete lut;
         return cuda_fail(e, "sb_build_lut: scratch allocation");
     }
-    LutLaunch L{src_guide, key_bits, n_bins, bounds, lut->entries, lut->src_packed, s};
+    LutLaunch L{src_guide, key_bits, key_channels, n_bins, bounds, lut->entries,
+                lut->src_packed, s};
     dispatch_format(src_guide->channels, src_guide->bits, L);
     e = cudaGetLastError();
     cudaFreeAsync(bounds, s);
@@ -281,6 +291,15 @@ extern "C" sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, s
     return ok();
 }
 
+extern "C" sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, sb_lut **out,
+                                  sb_stream stream) {
+    const int32_t channels = src_guide ? src_guide->channels : 0;
+    if (!src_guide) return fail(SB_ERR_INVALID_ARG, "src_guide: NULL guide descriptor");
+    if (channels >= 1 && channels * key_bits > kMaxKeyBitsTotal && key_bits >= 1)
+        return fail(SB_ERR_INVALID_ARG, "channels * key_bits must be <= 24");
+    return sb_build_lut_keyed(src_guide, key_bits, channels, out, stream);
+}
+
 extern "C" sb_status sb_lut_destroy(sb_lut *lut) {
     if (!lut) return ok();
     cudaError_t e = cudaFree(lut->entries);
@@ -293,8 +312,10 @@ extern "C" sb_status sb_lut_destroy(sb_lut *lut) {
 
 extern "C" sb_status sb_lut_info(const sb_lut *lut, const uint32_t **entries, int64_t *n_entries,
                                  int32_t *channels, int32_t *bits, int32_t *key_bits,
-                                 int32_t *src_width, int32_t *src_height) {
+                                 int32_t *key_channels, int32_t *src_width,
+                                 int32_t *src_height) {
     if (!lut) return fail(SB_ERR_INVALID_ARG, "lut: NULL");
+    if (key_channels) *key_channels = lut->key_channels;
     if (entries) *entries = lut->entries;
     if (n_entries) *n_entries = lut->n_entries;
     if (channels) *channels = lut->channels;
@@ -370,7 +391,7 @@ extern "C" sb_status sb_build_lut_noalloc(const sb_guide *src_guide, int32_t key
     if ((e = static_bounds_address(&bounds)) != cudaSuccess)
         return cuda_fail(e, "sb_build_lut_noalloc: scratch address");
     const uint32_t n_bins = 1u << (src_guide->channels * key_bits);
-    LutLaunch L{src_guide, key_bits, n_bins, bounds, table_out, nullptr,
+    LutLaunch L{src_guide, key_bits, src_guide->channels, n_bins, bounds, table_out, nullptr,
                 static_cast<cudaStream_t>(stream)};
     dispatch_format(src_guide->channels, src_guide->bits, L);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "sb_build_lut_noalloc: launch");

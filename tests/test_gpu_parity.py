@@ -252,3 +252,42 @@ def test_lookup_only_full_size_sampled(cuda_device):
     for x, y in zip(xs, ys):
         e = oracle.lut_entry(ex.guide, ex.lut_bits, oracle.lut_index(fr.guide, int(x), int(y), ex.lut_bits))
         assert (out[y, x] == ex.style[e >> 16, e & 0xFFFF]).all()
+
+
+# ---------------------------------------------------------------------------
+# extra guide channels (Section 4 segmentation guide): table keyed on the local guide
+# ---------------------------------------------------------------------------
+
+def _segmented(seed, H, W, Hs, Ws):
+    GT = synth.smooth_integer_guide(60 + seed, H, W, 4, step=4)
+    GS = synth.smooth_integer_guide(70 + seed, Hs, Ws, 4, step=4)
+    GT[..., 3] = np.where((np.arange(W)[None, :] // 17 + np.arange(H)[:, None] // 13) % 2, 255, 0)
+    GS[..., 3] = np.where(np.arange(Hs)[:, None] < Hs // 2, 0, 255)
+    return GT, GS
+
+
+@pytest.mark.parametrize("kc,kb", [(3, 5), (2, 7), (1, 8)])
+def test_keyed_table_matches_oracle(cuda_device, kc, kb):
+    _, GS = _segmented(1, 8, 8, 45, 53)
+    lut = sb.build_lut(to_dev(GS, cuda_device), kb, key_channels=kc)
+    assert lut.info()["key_channels"] == kc and lut.n_entries == 1 << (kc * kb)
+    got = lut.entries().cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, oracle.build_lut(GS, kb, key_channels=kc))
+
+
+@pytest.mark.parametrize("radius,T", [(0, 400), (2, 2500), (3, 6000)])
+def test_segmentation_guide_stylize_matches_oracle(cuda_device, radius, T):
+    GT, GS = _segmented(2, 97, 131, 48, 60)
+    style = synth.random_style(5, 48, 60)
+    gt, gs, st = to_dev(GT, cuda_device), to_dev(GS, cuda_device), to_dev(style, cuda_device)
+    lut = sb.build_lut(gs, 5, key_channels=3)
+    a, lev = sb.assign_chunks(gt, gs, lut, 5, T, 9)
+    out = sb.stylize(gt, gs, st, lut, 5, T, radius, 9)
+    torch.cuda.synchronize()
+    ref_out, ref_a, ref_lev = oracle.stylize(GT, GS, style, 5, 5, T, radius, 9, key_channels=3)
+    assert np.array_equal(u32(a), ref_a) and np.array_equal(lev.cpu().numpy(), ref_lev)
+    assert np.array_equal(out.cpu().numpy(), ref_out)
+    A = u32(a)
+    L = lev.cpu().numpy()
+    seg = GS[A >> 16, A & 0xFFFF, 3]
+    assert (seg[L > 1] == GT[..., 3][L > 1]).all()  # no chunk crosses a segment
