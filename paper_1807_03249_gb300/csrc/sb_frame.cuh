@@ -762,8 +762,12 @@ __device__ __forceinline__ void frame_tile(const FrameArgs &a, int tile_x, int t
     }
 }
 
+// CTAs per SM the kernels are compiled for: wide windows (R >= 3) spend more
+// of each tile waiting on loads, so they trade registers (64) for a fourth CTA.
+__host__ __device__ constexpr int min_ctas(int R) { return R >= 3 ? 4 : 3; }
+
 template <int C, int B, int MODE, int R>
-__global__ void __launch_bounds__(kThreads, 3) frame_kernel(const FrameArgs a) {
+__global__ void __launch_bounds__(kThreads, min_ctas(R)) frame_kernel(const FrameArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     frame_tile<C, B, MODE, R>(a, blockIdx.x, blockIdx.y, smem);
 }
@@ -783,7 +787,7 @@ struct BatchArgs {
 };
 
 template <int C, int B, int R>
-__global__ void __launch_bounds__(kThreads, 3) batch_kernel(const __grid_constant__ BatchArgs b) {
+__global__ void __launch_bounds__(kThreads, min_ctas(R)) batch_kernel(const __grid_constant__ BatchArgs b) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int t = (int)blockIdx.x;
     int lo = 0, hi = b.n - 1;  // last frame whose first tile is <= t
