@@ -117,23 +117,26 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def profiled_counters(workload: str) -> dict:
+    """Counters of one batch launch from the committed ncu summary, if it was
+    taken on the current kernel sources (else {})."""
     path = os.path.join(ROOT, "profiles", f"sb_stylize_batch_{workload}_traffic.txt")
     if not os.path.exists(path):
-        return None
+        return {}
     kv = {}
     for line in open(path):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
     if kv.get("kernel_source_hash") != kernel_source_hash():
-        return None
-    try:
-        return float(kv["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+        return {}
+    out = {}
+    for k in ("dram_bytes_per_launch", "warp_instructions_per_launch"):
+        try:
+            out[k] = float(kv[k])
+        except (KeyError, ValueError):
+            pass
+    return out
 
 
 def measured_peaks():
@@ -468,7 +471,17 @@ def run_gpu(args):
     kernel_s = ms_per_step / 1e3  # one batch launch per step
     alg = FRAMES_PER_STEP * ab["frame_bytes"] + ab["exemplar_bytes"]
     achieved = alg / kernel_s / 1e9
-    traffic = profiled_traffic(args.workload)
+    counters = profiled_counters(args.workload)
+    traffic = counters.get("dram_bytes_per_launch")
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = peaks.get("sm_max_mhz") or 2070.0
+    issue_peak = sm_count * 4 * sm_mhz * 1e6  # warp instructions per second
+    inst = counters.get("warp_instructions_per_launch")
+    issue = {"bound": "issue", "unit": "warp instructions/s", "peak": issue_peak,
+             "peak_rule": f"{sm_count} SMs x 4 issue slots x {sm_mhz:.0f} MHz",
+             "achieved": inst / kernel_s if inst else None,
+             "frac": inst / kernel_s / issue_peak if inst else None,
+             "instructions_per_launch": inst}
 
     line = {"metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -497,6 +510,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                     "api": "stylize_host per frame (pinned host in/out), 3 streams"},
+            "issue_roofline": issue,
             "per_frame_launch": per_frame,
             "lookup_only": lookup,
             "gpu_launches": args.steps,
@@ -551,6 +565,34 @@ def run_served(dev, n_requests: int = 10000, rate_hz: float = 2000.0, pool: int 
     reqs = [make(i, arrivals[0]) for i in range(n_requests)]
     done, wall = srv.run(reqs, real_time=True)
     out = latency_summary(done, wall)
+
+    # saturation: the same kind of requests all waiting at once, served by the
+    # continuous-batching loop vs one plain sb_stylize per request (with the
+    # same copies) on one stream
+    import paper_1807_03249_gb300 as sb
+    n_sat = min(2000, n_requests)
+    sat = [make(i, arrivals[0]) for i in range(n_sat)]
+    _, wall_sat = srv.run(sat, real_time=False)
+    px_sat = sum(r.pixels for r in sat)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for r in sat:
+            g = torch.empty(r.guide.shape, dtype=r.guide.dtype, device=dev)
+            g.copy_(r.guide, non_blocking=True)
+            gd, sd, lut = srv.exemplars[r.exemplar]
+            o = sb.stylize(g, gd, sd, lut, r.levels, r.threshold, 2, r.seed, stream=stream)
+            r.out.copy_(o, non_blocking=True)
+    torch.cuda.synchronize()
+    wall_seq = time.perf_counter() - t0
+    out["saturated"] = {"requests": n_sat,
+                        "batched_frames_per_s": n_sat / wall_sat,
+                        "batched_mpixel_per_s": px_sat / wall_sat / 1e6,
+                        "per_request_frames_per_s": n_sat / wall_seq,
+                        "per_request_mpixel_per_s": px_sat / wall_seq / 1e6,
+                        "what": "all requests waiting at t=0: serving loop (4 slots, groups of "
+                                "<= 16) vs one sb_stylize per request on one stream"}
     offered_px = sum(r.pixels for r in reqs) / float(arrivals[-1] - arrivals[0])
     out.update({"offered_req_per_s": rate_hz, "offered_mpixel_per_s": offered_px / 1e6,
                 "slots": 4, "max_batch": 16, "budget_gb": 40,
