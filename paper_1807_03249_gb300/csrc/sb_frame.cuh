@@ -6,23 +6,27 @@
 // assignment A of the tile plus a halo of R pixels (the vote window) in shared
 // memory, so A never reaches device memory:
 //
-//   phase 0  target guide of the region -> smem (one packed uint32 per pixel);
-//            the seed cells of every level >= 3 are built at the same time
-//            (levels 2 and 1 have many cells and are built only if a pixel of
-//            the tile still needs them).  A cell is: jitter hash -> seed q
-//            clamped into the target -> G_T[q] -> table entry u*(q).  Cells are
-//            stored column-major (x outer, y inner), each as (-2q, |q|^2, u*)
-//            in region-centred coordinates, pre-scaled by 2^11 with the cell's
-//            column-major index in the low 11 bits.
-//   levels   for l = L..1 while pixels are pending, each pending pixel p takes
-//            the minimum over its 3 x 3 cells of |q|^2 - 2 q.p (which orders
-//            seeds like |q - p|^2) packed with the cell index: one min gives
-//            the nearest seed and, on ties, the first cell in x-outer,
-//            y-inner order, as NearestSeed's strict < does.  The candidate
+//   phase 0  target guide of the region -> smem (one packed uint32 per pixel),
+//            read by vertical segments of 4 pixels (one region column per
+//            lane); the seed cells of every level >= 3 are built at the same
+//            time (levels 2 and 1 have many cells and are built only if a
+//            pixel of the tile still needs them).  A cell is: jitter hash ->
+//            seed q clamped into the target -> G_T[q] -> table entry u*(q).
+//            Cells are stored column-major (x outer, y inner), each as
+//            (-2q, |q|^2, u*) in region-centred coordinates, pre-scaled by
+//            2^11 with the cell's column-major index in the low 11 bits.
+//   levels   for l = L..1 while pixels are pending: a pixel p takes the
+//            minimum over its 3 x 3 cells of |q|^2 - 2 q.p (which orders seeds
+//            like |q - p|^2) packed with the cell index: one min gives the
+//            nearest seed and, on ties, the first cell in x-outer, y-inner
+//            order, as NearestSeed's strict < does.  The candidate
 //            s = u* + (p - q) is accepted if it lies in the source and
 //            |G_S[s] - G_T[p]|^2 <= t (level 1 always accepts, s clamped).
-//            Pixels go four per thread per batch with their gathers issued
-//            first; rejected ones are compacted into the next pending list.
+//            Work goes by the 4-pixel segments: a segment lies in one cell at
+//            levels >= 2 and the pixels choosing a seed form a convex set, so
+//            when its first and last pending pixels choose the same seed all
+//            of them do and the search runs once.  Segments with rejected
+//            pixels are compacted into the next level's list.
 //   vote     ballot bitmasks mark, per row, where A steps by exactly one pixel
 //            (horizontally and vertically); a window made of one translation
 //            votes exactly C_S[A(p)], a plain copy.  Other pixels (chunk
@@ -220,101 +224,189 @@ __device__ __forceinline__ int4 nearest_cell(const int4 *cells, int base, int c0
     return cl;
 }
 
-// Top level over horizontal pixel pairs (x even, x + 1): the two pixels share
-// their cell at every level, so one pass over the nine candidates gives both
-// packed keys (the right key is the left key plus the candidate's x slope).
-// Accepted pixels get A (and the level); rejected ones are appended to list_out.
-template <int C, int B, int R>
-__device__ __forceinline__ void top_level_pairs(const FrameArgs &a, const uint32_t *gt,
-                                                uint32_t *A, uint8_t *lev, const int4 *cells,
-                                                const LevelCells &g, int l, int rx0, int ry0,
-                                                uint32_t t32, uint16_t *list_out,
-                                                int *cnt_out) {
+// Vertical segments of 4 pixels starting at target rows that are multiples of
+// 4 cover the region (the tile plus its R halo): segment s takes region column
+// s % RW, so the lanes of a warp hold neighbouring columns.  At every level
+// >= 2 a segment lies inside one seed cell.
+template <int R>
+struct Segs {
+    static constexpr int kPad = (R + 3) / 4 * 4;  // first segment row: kPad rows above the tile
+    static constexpr int RW = kTW + 2 * R, RH = kTH + 2 * R;
+    static constexpr int NSY = (kTH + 2 * kPad) / 4;
+    static constexpr int NS = RW * NSY;
+    __device__ __forceinline__ static int rx(int s) { return s % RW; }
+    __device__ __forceinline__ static int ry(int s) { return 4 * (s / RW) - kPad + R; }
+    // bit j: row ry + j lies in the region
+    __device__ __forceinline__ static uint32_t rows(int ry) {
+        uint32_t m = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m |= (uint32_t)(ry + j >= 0 && ry + j < RH) << j;
+        return m;
+    }
+    // bit j: pixel (rx, ry + j) lies in the region and in the W x H target
+    __device__ __forceinline__ static uint32_t mask(int rx, int ry, int rx0, int ry0, int W,
+                                                    int H) {
+        const bool col = rx0 + rx >= 0 && rx0 + rx < W;
+        uint32_t m = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int y = ry + j;
+            m |= (uint32_t)(col && y >= 0 && y < RH && ry0 + y >= 0 && ry0 + y < H) << j;
+        }
+        return m;
+    }
+};
+
+// Candidate test of the pixels of one segment: pixel j sits at region index
+// ibase + j * RW and its candidate source position is (sx[j], sy[j]).
+// Accepted pixels get A (and the level); the bits of rejected pixels of m
+// are returned.
+template <int C, int B, int RW>
+__device__ __forceinline__ uint32_t test_segment(const FrameArgs &a, const uint32_t *gt,
+                                                 uint32_t *A, uint8_t *lev, int l, uint32_t t32,
+                                                 uint32_t m, int ibase, const int (&sx)[4],
+                                                 const int (&sy)[4]) {
     using F = GuideFmt<C, B>;
-    constexpr int RW = kTW + 2 * R, RH = kTH + 2 * R;
-    constexpr int PR = RW / 2 + (R & 1);  // pairs per region row (x0 - R is odd for odd R)
-    constexpr int NP = PR * RH;
-    constexpr int kPairs = 2;             // pairs per thread per batch
-    constexpr int kPx = 2 * kPairs;
-    for (int j0 = 0; j0 < NP; j0 += kThreads * kPairs) {
-        int idx[kPx];
-        uint32_t sv[kPx], gsv[kPx];
-        bool act[kPx], inb[kPx];
+    uint32_t gsv[4];
+    bool ok[4];
 #pragma unroll
-        for (int u = 0; u < kPairs; ++u) {
-            const int jp = j0 + u * kThreads + threadIdx.x;
-            const int ry = jp / PR, rxl = 2 * (jp - ry * PR) - (R & 1);
-            const int il = ry * RW + rxl;
-            bool aL = false, aR = false;
-            if (jp < NP) {
-                aL = rxl >= 0 && A[il] == kPending;
-                aR = rxl + 1 < RW && A[il + 1] == kPending;
-            }
-            act[2 * u] = aL;
-            act[2 * u + 1] = aR;
-            idx[2 * u] = aL ? il : 0;
-            idx[2 * u + 1] = aR ? il + 1 : 0;
+    for (int j = 0; j < 4; ++j) {
+        ok[j] = ((m >> j) & 1u) && (unsigned)sx[j] < (unsigned)a.Ws &&
+                (unsigned)sy[j] < (unsigned)a.Hs;
+        gsv[j] = ok[j] ? __ldg(a.src_packed + (int64_t)sy[j] * a.Ws + sx[j]) : 0u;
+    }
+    uint32_t rej = 0;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                inb[2 * u + h] = false;
-                gsv[2 * u + h] = 0;
-                sv[2 * u + h] = 0;
-            }
-            if (aL || aR) {
-                const int prl = rxl - RW / 2, pry = ry - RH / 2;
-                // both pixels lie in the cell of the right one's column
-                const int lcx = ((rx0 + rxl + 1) >> l) - g.cx0, lcy = ((ry0 + ry) >> l) - g.cy0;
-                const int c0 = lcx * g.ncy + lcy;
-                int kl = INT_MAX, kr = INT_MAX;
+    for (int j = 0; j < 4; ++j) {
+        if (!((m >> j) & 1u)) continue;
+        bool acc = false;
+        if (ok[j]) {
+            const uint64_t d = F::dist(gsv[j], gt[ibase + j * RW]);
+            if constexpr (B == 8) acc = (uint32_t)d <= t32;
+            else acc = d <= a.threshold;
+        }
+        if (acc) {
+            A[ibase + j * RW] = (uint32_t)sx[j] + ((uint32_t)sy[j] << 16);
+            if (lev) lev[ibase + j * RW] = (uint8_t)l;
+        }
+        rej |= (uint32_t)!acc << j;
+    }
+    return rej;
+}
+
+// Level l (1 <= l <= kPackedMaxLevel) of the pixels m of the segment at
+// region (rx, ry): returns the rejected ones.  The packed keys of the nine
+// candidates are affine in p, so the pixels that pick a given seed form a
+// convex set: when the first and last pixel of m pick the same seed, every
+// pixel between them does and the nine-way search runs once.  Otherwise (and
+// at level 1, where the segment spans two cells) each pixel searches.
+template <int C, int B, int R>
+__device__ __forceinline__ uint32_t segment_level(const FrameArgs &a, const uint32_t *gt,
+                                                  uint32_t *A, uint8_t *lev, const int4 *cells,
+                                                  int base, const LevelCells &g, int l, int rx0,
+                                                  int ry0, uint32_t t32, int rx, int ry,
+                                                  uint32_t m) {
+    using S = Segs<R>;
+    constexpr int RW = S::RW, RH = S::RH;
+    constexpr int kMask = (1 << kKeyShift) - 1;
+    const int prx = rx - RW / 2, pry = ry - RH / 2;
+    const int c0 = base + (((rx0 + rx) >> l) - g.cx0) * g.ncy + (((ry0 + ry) >> l) - g.cy0);
+    const int ibase = ry * RW + rx;
+    int sx[4], sy[4];
+    auto candidate = [&](int j, int key) {
+        const int4 cl = cells[base + (key & kMask)];
+        sx[j] = (int)((uint32_t)cl.w & 0xFFFFu) + prx + (cl.x >> (kKeyShift + 1));
+        sy[j] = (int)((uint32_t)cl.w >> 16) + pry + j + (cl.y >> (kKeyShift + 1));
+    };
+    if (l == 1) {
+        // rows 0-1 and 2-3 lie in consecutive cells of one column
 #pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
+        for (int j = 0; j < 4; ++j) {
+            if (!((m >> j) & 1u)) continue;
+            int key = INT_MAX;
 #pragma unroll
-                    for (int dy = -1; dy <= 1; ++dy) {
-                        const int4 cl = cells[c0 + dx * g.ncy + dy];
-                        const int e = cl.z + cl.x * prl + cl.y * pry;
-                        kl = min(kl, e);
-                        kr = min(kr, e + cl.x);
-                    }
+            for (int dx = -1; dx <= 1; ++dx) {
+#pragma unroll
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int4 cl = cells[c0 + (j >> 1) + dx * g.ncy + dy];
+                    key = min(key, cl.z + cl.x * prx + cl.y * (pry + j));
                 }
+            }
+            candidate(j, key);
+            const int x = min(max(sx[j], 0), a.Ws - 1), y = min(max(sy[j], 0), a.Hs - 1);
+            A[ibase + j * RW] = (uint32_t)x | ((uint32_t)y << 16);
+            if (lev) lev[ibase + j * RW] = 1;
+        }
+        return 0;
+    }
+    const int jlo = __ffs(m) - 1, jhi = 31 - __clz(m);
+    int klo = INT_MAX, khi = INT_MAX;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (!(h ? aR : aL)) continue;
-                    const int4 cl = cells[(h ? kr : kl) & ((1 << kKeyShift) - 1)];
-                    int sx = (int)((uint32_t)cl.w & 0xFFFFu) + prl + h + (cl.x >> (kKeyShift + 1));
-                    int sy = (int)((uint32_t)cl.w >> 16) + pry + (cl.y >> (kKeyShift + 1));
-                    if (l > 1) {
-                        inb[2 * u + h] =
-                            (unsigned)sx < (unsigned)a.Ws && (unsigned)sy < (unsigned)a.Hs;
-                        if (inb[2 * u + h])
-                            gsv[2 * u + h] = __ldg(a.src_packed + (int64_t)sy * a.Ws + sx);
-                    } else {
-                        sx = min(max(sx, 0), a.Ws - 1);
-                        sy = min(max(sy, 0), a.Hs - 1);
-                    }
-                    sv[2 * u + h] = (uint32_t)sx | ((uint32_t)sy << 16);
-                }
+    for (int dx = -1; dx <= 1; ++dx) {
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int4 cl = cells[c0 + dx * g.ncy + dy];
+            const int e = cl.z + cl.x * prx + cl.y * (pry + jlo);
+            klo = min(klo, e);
+            khi = min(khi, e + (jhi - jlo) * cl.y);
+        }
+    }
+    if (((klo ^ khi) & kMask) == 0) {
+        candidate(0, klo);
+#pragma unroll
+        for (int j = 1; j < 4; ++j) {
+            sx[j] = sx[0];
+            sy[j] = sy[0] + j;
+        }
+    } else {
+        int k[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int4 cl = cells[c0 + dx * g.ncy + dy];
+                const int e = cl.z + cl.x * prx + cl.y * pry;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) k[j] = min(k[j], e + j * cl.y);
             }
         }
 #pragma unroll
-        for (int k = 0; k < kPx; ++k) {
-            bool acc = false;
-            if (act[k]) {
-                if (l > 1) {
-                    if (inb[k]) {
-                        const uint64_t d = F::dist(gsv[k], gt[idx[k]]);
-                        if constexpr (B == 8) acc = (uint32_t)d <= t32;
-                        else acc = d <= a.threshold;
-                    }
-                } else {
-                    acc = true;
-                }
-                if (acc) {
-                    A[idx[k]] = sv[k];
-                    if (lev) lev[idx[k]] = (uint8_t)l;
-                }
+        for (int j = 0; j < 4; ++j) candidate(j, k[j]);
+    }
+    return test_segment<C, B, RW>(a, gt, A, lev, l, t32, m, ibase, sx, sy);
+}
+
+// One level over segments: the top level visits every segment of the region
+// (its in-target pixels), lower levels the list of segments with pending
+// pixels (entries: segment index << 4 | pixel mask).  Segments with rejected
+// pixels are appended to list_out.
+template <int C, int B, int R, bool kTop>
+__device__ __forceinline__ void level_segments(const FrameArgs &a, const uint32_t *gt,
+                                               uint32_t *A, uint8_t *lev, const int4 *cells,
+                                               int base, const LevelCells &g, int l, int rx0,
+                                               int ry0, uint32_t t32, const uint16_t *list_in,
+                                               int n_in, uint16_t *list_out, int *cnt_out) {
+    using S = Segs<R>;
+    const int n = kTop ? S::NS : n_in;
+    for (int s0 = 0; s0 < n; s0 += kThreads) {
+        const int jj = s0 + (int)threadIdx.x;
+        int sg = 0;
+        uint32_t m = 0;
+        if (jj < n) {
+            if constexpr (kTop) {
+                sg = jj;
+                m = S::mask(S::rx(sg), S::ry(sg), rx0, ry0, a.W, a.H);
+            } else {
+                const uint32_t e = list_in[jj];
+                sg = (int)(e >> 4);
+                m = e & 15u;
             }
-            list_push(act[k] && !acc, idx[k], list_out, cnt_out);
         }
+        uint32_t rej = 0;
+        if (m)
+            rej = segment_level<C, B, R>(a, gt, A, lev, cells, base, g, l, rx0, ry0, t32,
+                                         S::rx(sg), S::ry(sg), m);
+        list_push(rej != 0, (sg << 4) | (int)rej, list_out, cnt_out);
     }
 }
 
@@ -341,35 +433,69 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     const int L_top = a.levels;
     const int eager_lo = L_top <= kEagerMinLevel ? 1 : kEagerMinLevel;
 
+    // with 2 <= L <= kPackedMaxLevel every level goes by segments (the lists
+    // hold segments with pending pixels); otherwise by lists of pixels
+    const bool seg_mode = L_top >= 2 && L_top <= kPackedMaxLevel;
     if (tid == 0) {
         cnt[0] = 0;
         cnt[1] = 0;
     }
-#pragma unroll 4
-    for (int i = tid; i < NR; i += kThreads) {
-        const int gx = rx0 + i % RW, gy = ry0 + i / RW;
-        const bool inside = gx >= 0 && gy >= 0 && gx < a.W && gy < a.H;
-        gt[i] = inside ? F::load(a.tgt, a.tgt_stride, gx, gy) : 0u;
-        A[i] = inside ? kPending : kInvalid;
+    for (int sg = tid; sg < Segs<R>::NS; sg += kThreads) {
+        const int rx = Segs<R>::rx(sg), ry = Segs<R>::ry(sg);
+        const uint32_t rl = Segs<R>::rows(ry);
+        const uint32_t it = Segs<R>::mask(rx, ry, rx0, ry0, a.W, a.H);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!((rl >> j) & 1u)) continue;
+            const int i = (ry + j) * RW + rx;
+            if ((it >> j) & 1u) {
+                gt[i] = F::load(a.tgt, a.tgt_stride, rx0 + rx, ry0 + ry + j);
+                if (!seg_mode) A[i] = kPending;
+            } else {
+                A[i] = kInvalid;
+            }
+        }
     }
     build_cells<C, B>(a, cells, L_top, eager_lo, 0, xa, xb, ya, yb, cxo, cyo);
     __syncthreads();
 
+    if (seg_mode) {
+        int n_pend, base, cur = 1;
+        {
+            // top level over every segment (cells of the top level start at 0)
+            const LevelCells g = level_cells(L_top, xa, xb, ya, yb);
+            level_segments<C, B, R, true>(a, gt, A, lev, cells, 0, g, L_top, rx0, ry0, t32,
+                                          nullptr, 0, list1, &cnt[1]);
+            __syncthreads();
+            n_pend = cnt[1];
+            base = g.ncx * g.ncy;
+            __syncthreads();  // every thread has read cnt[1] before the next level writes cnt[0]
+        }
+        for (int l = L_top - 1; l >= 1 && n_pend > 0; --l) {
+            const LevelCells g = level_cells(l, xa, xb, ya, yb);
+            if (l == kEagerMinLevel - 1 && eager_lo > 1) {
+                // a pixel still needs the fine levels: build levels 2 and 1 now
+                build_cells<C, B>(a, cells, l, 1, base, xa, xb, ya, yb, cxo, cyo);
+                __syncthreads();
+            }
+            const int nxt = cur ^ 1;
+            level_segments<C, B, R, false>(a, gt, A, lev, cells, base, g, l, rx0, ry0, t32,
+                                           cur ? list1 : list0, n_pend, cur ? list0 : list1,
+                                           &cnt[nxt]);
+            __syncthreads();
+            n_pend = cnt[nxt];
+            if (tid == 0) cnt[cur] = 0;  // see the pixel-list loop below
+            base += g.ncx * g.ncy;
+            __syncthreads();
+            cur = nxt;
+        }
+        return;
+    }
+
     int cur = 0;
     int n_pend = NR;  // the top level scans the whole region
     int base = 0;     // first cell of the current level
-    int l_start = L_top;
-    if (L_top <= kPackedMaxLevel) {
-        // top level by pixel pairs (cells of the top level start at 0)
-        const LevelCells g = level_cells(L_top, xa, xb, ya, yb);
-        top_level_pairs<C, B, R>(a, gt, A, lev, cells, g, L_top, rx0, ry0, t32, list1, &cnt[1]);
-        __syncthreads();
-        n_pend = cnt[1];
-        base = g.ncx * g.ncy;
-        cur = 1;
-        l_start = L_top - 1;
-        __syncthreads();  // every thread has read cnt[1] before the next level writes cnt[0]
-    }
+    const int l_start = L_top;
     for (int l = l_start; l >= 1 && n_pend > 0; --l) {
         const LevelCells g = level_cells(l, xa, xb, ya, yb);
         if (l == kEagerMinLevel - 1 && eager_lo > 1) {
