@@ -141,47 +141,72 @@ __device__ __forceinline__ LevelCells level_cells(int l, int xa, int xb, int ya,
     return g;
 }
 
-// Builds the cells of levels l_hi down to l_lo into cells[base_hi...]; the
-// levels are stacked from l_hi downwards, each column-major.
-template <int C, int B>
-__device__ __forceinline__ void build_cells(const FrameArgs &a, int4 *cells, int l_hi, int l_lo,
-                                            int base_hi, int xa, int xb, int ya, int yb,
-                                            int cxo, int cyo) {
-    using F = GuideFmt<C, B>;
+// Number of cells of levels l_hi down to l_lo for the clamped region.
+__device__ __forceinline__ int cell_count(int l_hi, int l_lo, int xa, int xb, int ya, int yb) {
     int total = 0;
     for (int l = l_hi; l >= l_lo; --l) {
         const LevelCells g = level_cells(l, xa, xb, ya, yb);
         total += g.ncx * g.ncy;
     }
+    return total;
+}
+
+// Cell k of the levels stacked from l_hi downwards (each column-major): its
+// level, column-major index within the level and seed q (clamped into the
+// target).
+struct CellTask {
+    int l, ci, sx, sy;
+};
+
+__device__ __forceinline__ CellTask cell_task(const FrameArgs &a, int k, int l_hi, int xa, int xb,
+                                              int ya, int yb) {
+    CellTask t;
+    int l = l_hi, off = 0;
+    LevelCells g = level_cells(l, xa, xb, ya, yb);
+    while (k >= off + g.ncx * g.ncy) {
+        off += g.ncx * g.ncy;
+        --l;
+        g = level_cells(l, xa, xb, ya, yb);
+    }
+    const int ci = k - off;  // column-major: ci = lcx * ncy + lcy
+    const int lcx = ci / g.ncy, lcy = ci - lcx * g.ncy;
+    const int h = 1 << l;
+    const int bx = g.cx0 + lcx, by = g.cy0 + lcy;
+    const uint32_t hsh = cell_hash(level_key(a.seed, l), bx, by);
+    const int ox = (int)(((hsh & 0xFFFFu) * (uint32_t)h) >> 16);
+    const int oy = (int)(((hsh >> 16) * (uint32_t)h) >> 16);
+    t.l = l;
+    t.ci = ci;
+    t.sx = min(max(bx * h + ox, 0), a.W - 1);
+    t.sy = min(max(by * h + oy, 0), a.H - 1);
+    return t;
+}
+
+// The stored cell: (-2q, |q|^2, u*) in region-centred coordinates (q - (cxo,
+// cyo)); levels with packed keys scale by 2^11 and add the cell index.
+__device__ __forceinline__ int4 cell_value(const CellTask &t, uint32_t u, int cxo, int cyo) {
+    const int qx = t.sx - cxo, qy = t.sy - cyo;
+    if (t.l <= kPackedMaxLevel) {
+        constexpr int S = 1 << kKeyShift;
+        return make_int4(-2 * qx * S, -2 * qy * S, (qx * qx + qy * qy) * S + t.ci, (int)u);
+    }
+    return make_int4(-2 * qx, -2 * qy, qx * qx + qy * qy, (int)u);
+}
+
+// Builds cells k0, k0 + kThreads, ... of the levels l_hi down to l_lo into
+// cells[base_hi + k].
+template <int C, int B>
+__device__ __forceinline__ void build_cells(const FrameArgs &a, int4 *cells, int l_hi, int l_lo,
+                                            int base_hi, int xa, int xb, int ya, int yb,
+                                            int cxo, int cyo, int k0 = 0) {
+    using F = GuideFmt<C, B>;
+    const int total = cell_count(l_hi, l_lo, xa, xb, ya, yb);
 #pragma unroll 2
-    for (int k = threadIdx.x; k < total; k += kThreads) {
-        int l = l_hi, off = 0;
-        LevelCells g = level_cells(l, xa, xb, ya, yb);
-        while (k >= off + g.ncx * g.ncy) {
-            off += g.ncx * g.ncy;
-            --l;
-            g = level_cells(l, xa, xb, ya, yb);
-        }
-        const int ci = k - off;               // column-major: ci = lcx * ncy + lcy
-        const int lcx = ci / g.ncy, lcy = ci - lcx * g.ncy;
-        const int h = 1 << l;
-        const int bx = g.cx0 + lcx, by = g.cy0 + lcy;
-        const uint32_t hsh = cell_hash(level_key(a.seed, l), bx, by);
-        const int ox = (int)(((hsh & 0xFFFFu) * (uint32_t)h) >> 16);
-        const int oy = (int)(((hsh >> 16) * (uint32_t)h) >> 16);
-        const int sx = min(max(bx * h + ox, 0), a.W - 1);
-        const int sy = min(max(by * h + oy, 0), a.H - 1);
-        const uint32_t u =
-            __ldg(a.lut + F::key(F::load(a.tgt, a.tgt_stride, sx, sy), a.key_bits, a.key_channels));
-        const int qx = sx - cxo, qy = sy - cyo;
-        int4 cell;
-        if (l <= kPackedMaxLevel) {
-            constexpr int S = 1 << kKeyShift;
-            cell = make_int4(-2 * qx * S, -2 * qy * S, (qx * qx + qy * qy) * S + ci, (int)u);
-        } else {
-            cell = make_int4(-2 * qx, -2 * qy, qx * qx + qy * qy, (int)u);
-        }
-        cells[base_hi + k] = cell;
+    for (int k = k0 + (int)threadIdx.x; k < total; k += kThreads) {
+        const CellTask t = cell_task(a, k, l_hi, xa, xb, ya, yb);
+        const uint32_t u = __ldg(
+            a.lut + F::key(F::load(a.tgt, a.tgt_stride, t.sx, t.sy), a.key_bits, a.key_channels));
+        cells[base_hi + k] = cell_value(t, u, cxo, cyo);
     }
 }
 
@@ -440,7 +465,34 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
         cnt[0] = 0;
         cnt[1] = 0;
     }
-    for (int sg = tid; sg < Segs<R>::NS; sg += kThreads) {
+    // phase 0: every global load (the guide at this thread's first seed, the
+    // region's guide, then the seed's table entry) is issued before the
+    // first store that waits on one
+    const int n_eager = cell_count(L_top, eager_lo, xa, xb, ya, yb);
+    const bool has_cell = tid < n_eager;
+    CellTask ct{};
+    uint32_t cg = 0;
+    if (has_cell) {
+        ct = cell_task(a, tid, L_top, xa, xb, ya, yb);
+        cg = F::load(a.tgt, a.tgt_stride, ct.sx, ct.sy);
+    }
+    constexpr int kSegIters = (Segs<R>::NS + kThreads - 1) / kThreads;
+    uint32_t gv[kSegIters][4];
+#pragma unroll
+    for (int q = 0; q < kSegIters; ++q) {
+        const int sg = q * kThreads + tid;
+        const int rx = Segs<R>::rx(sg), ry = Segs<R>::ry(sg);
+        const uint32_t it = sg < Segs<R>::NS ? Segs<R>::mask(rx, ry, rx0, ry0, a.W, a.H) : 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            gv[q][j] = ((it >> j) & 1u) ? F::load(a.tgt, a.tgt_stride, rx0 + rx, ry0 + ry + j) : 0u;
+    }
+    uint32_t cu = 0;
+    if (has_cell) cu = __ldg(a.lut + F::key(cg, a.key_bits, a.key_channels));
+#pragma unroll
+    for (int q = 0; q < kSegIters; ++q) {
+        const int sg = q * kThreads + tid;
+        if (sg >= Segs<R>::NS) continue;
         const int rx = Segs<R>::rx(sg), ry = Segs<R>::ry(sg);
         const uint32_t rl = Segs<R>::rows(ry);
         const uint32_t it = Segs<R>::mask(rx, ry, rx0, ry0, a.W, a.H);
@@ -449,14 +501,15 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
             if (!((rl >> j) & 1u)) continue;
             const int i = (ry + j) * RW + rx;
             if ((it >> j) & 1u) {
-                gt[i] = F::load(a.tgt, a.tgt_stride, rx0 + rx, ry0 + ry + j);
+                gt[i] = gv[q][j];
                 if (!seg_mode) A[i] = kPending;
             } else {
                 A[i] = kInvalid;
             }
         }
     }
-    build_cells<C, B>(a, cells, L_top, eager_lo, 0, xa, xb, ya, yb, cxo, cyo);
+    if (has_cell) cells[tid] = cell_value(ct, cu, cxo, cyo);
+    build_cells<C, B>(a, cells, L_top, eager_lo, 0, xa, xb, ya, yb, cxo, cyo, kThreads);
     __syncthreads();
 
     if (seg_mode) {
