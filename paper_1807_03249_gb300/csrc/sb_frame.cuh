@@ -32,7 +32,8 @@
 //            votes exactly C_S[A(p)], a plain copy.  Other pixels (chunk
 //            boundaries, frame borders) are compacted and summed over the full
 //            window with integer sums and round-half-up division.
-//   store    the tile leaves shared memory with coalesced 32-bit stores.
+//   store    uniform windows store from the copy pass (coalesced rows), the
+//            others from the full-window passes.
 #pragma once
 
 #include <atomic>
@@ -689,8 +690,7 @@ __device__ __forceinline__ uint32_t div_round(uint32_t s, uint32_t n, uint32_t m
 }
 
 template <bool F32, typename Acc>
-__device__ __forceinline__ void vote_store(const FrameArgs &a, const Acc &acc, int gx, int gy,
-                                           int k, uint32_t *out_tile) {
+__device__ __forceinline__ void vote_store(const FrameArgs &a, const Acc &acc, int gx, int gy) {
     uint32_t s0, s1, s2, s3;
     acc.sums(s0, s1, s2, s3);
     const uint32_t n = acc.n;
@@ -709,7 +709,7 @@ __device__ __forceinline__ void vote_store(const FrameArgs &a, const Acc &acc, i
             o = div_round(s0, n, m) | (div_round(s1, n, m) << 8) | (div_round(s2, n, m) << 16) |
                 (div_round(s3, n, m) << 24);
         }
-        out_tile[k] = o;
+        a.rgba_out[(int64_t)gy * a.W + gx] = o;
     }
 }
 
@@ -726,7 +726,7 @@ template <int R, bool F32>
 __device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const uint32_t *A,
                                                const uint32_t *E, const uint16_t *slow,
                                                int n_slow, uint16_t *cplx, int *cplx_cnt,
-                                               int x0, int y0, uint32_t *out_tile) {
+                                               int x0, int y0) {
     constexpr int RW = kTW + 2 * R;
     constexpr bool kPacked = (2 * R + 1) * (2 * R + 1) * 255 < 65536;
     constexpr uint32_t kBreakMask = (2 * R >= 32) ? 0xFFFFFFFFu : ((1u << (2 * R)) - 1u);
@@ -766,7 +766,7 @@ __device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const uint32_
                 tap(acc, row, tx, min(tx + j1 + 1, tx + 2 * R), oy,
                     pc == 1 ? (uint32_t)(2 * R - j1) : 0u);
             }
-            if (!complex_row) vote_store<F32>(a, acc, x0 + tx, y0 + ty, k, out_tile);
+            if (!complex_row) vote_store<F32>(a, acc, x0 + tx, y0 + ty);
         }
         list_push(act && complex_row, k, cplx, cplx_cnt);
     }
@@ -781,7 +781,7 @@ __device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const uint32_
 #pragma unroll
             for (int ox = 0; ox <= 2 * R; ++ox) tap(acc, row, tx, tx + ox, oy, 1u);
         }
-        vote_store<F32>(a, acc, x0 + tx, y0 + ty, k, out_tile);
+        vote_store<F32>(a, acc, x0 + tx, y0 + ty);
     }
 }
 
@@ -792,8 +792,7 @@ __device__ __forceinline__ uint64_t shr128(uint64_t lo, uint64_t hi, int j) {
 
 template <int R, bool F32>
 __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &L, int x0,
-                                          int y0, const uint32_t *A, unsigned char *smem,
-                                          uint32_t *out_tile) {
+                                          int y0, const uint32_t *A, unsigned char *smem) {
     constexpr int RW = kTW + 2 * R, RH = kTH + 2 * R;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint64_t *hu_row = reinterpret_cast<uint64_t *>(smem + L.off_masks);
@@ -891,7 +890,7 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
                 if constexpr (F32) {
                     a.f32_out[(int64_t)(y0 + ty) * a.W + x0 + tx] = rgba_f32(col[q][c]);
                 } else {
-                    out_tile[k] = col[q][c];
+                    a.rgba_out[(int64_t)(y0 + ty) * a.W + x0 + tx] = col[q][c];
                 }
             }
             list_push(need[q][c], k, slow, slow_cnt);
@@ -900,7 +899,7 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
     __syncthreads();
     vote_slow_list<R, F32>(a, A, E_row, slow, *slow_cnt,
                            reinterpret_cast<uint16_t *>(smem + L.off_list1), slow_cnt + 1, x0,
-                           y0, out_tile);
+                           y0);
 }
 
 // One 64 x 32 output tile (tile_x, tile_y) of one frame.
@@ -926,18 +925,7 @@ __device__ __forceinline__ void frame_tile(const FrameArgs &a, int tile_x, int t
             }
         }
     } else {
-        // the target guide is no longer needed: its slot holds the output tile
-        uint32_t *out_tile = reinterpret_cast<uint32_t *>(smem + L.off_gt);
-        vote_tile<R, false>(a, L, x0, y0, A, smem, out_tile);
-        __syncthreads();
-        for (int ty = warp; ty < kTH; ty += kWarps) {
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int tx = c * 32 + lane;
-                const int gx = x0 + tx, gy = y0 + ty;
-                if (gx < a.W && gy < a.H) a.rgba_out[(int64_t)gy * a.W + gx] = out_tile[ty * kTW + tx];
-            }
-        }
+        vote_tile<R, false>(a, L, x0, y0, A, smem);
     }
 }
 
@@ -995,20 +983,7 @@ __global__ void __launch_bounds__(kThreads) blend_kernel(const FrameArgs a) {
         A[i] = inside ? __ldg(a.assign_in + (int64_t)gy * a.W + gx) : kInvalid;
     }
     __syncthreads();
-    uint32_t *out_tile = reinterpret_cast<uint32_t *>(smem + L.off_gt);
-    vote_tile<R, F32>(a, L, x0, y0, A, smem, out_tile);
-    if constexpr (!F32) {
-        __syncthreads();
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int ty = warp; ty < kTH; ty += kWarps) {
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int tx = c * 32 + lane;
-                const int gx = x0 + tx, gy = y0 + ty;
-                if (gx < a.W && gy < a.H) a.rgba_out[(int64_t)gy * a.W + gx] = out_tile[ty * kTW + tx];
-            }
-        }
-    }
+    vote_tile<R, F32>(a, L, x0, y0, A, smem);
 }
 
 // Raises a kernel's dynamic shared-memory limit once per (kernel, device);

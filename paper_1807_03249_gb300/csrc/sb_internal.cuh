@@ -104,9 +104,10 @@ struct GuideFmt {
     // squared Euclidean guide distance; fits 32 bits except 16-bit x 2
     __device__ __forceinline__ static uint64_t dist(uint32_t a, uint32_t b) {
         if constexpr (B == 8) {
-            // |a - b|^2 = |a|^2 + |b|^2 - 2 a.b with 4-way byte dot products
-            // (unused channels are zero in both); exact in 32 bits
-            return __dp4a(a, a, 0u) + __dp4a(b, b, 0u) - 2u * __dp4a(a, b, 0u);
+            // per-byte |a - b|, then the 4-way byte dot product of that with
+            // itself (unused channels are zero in both); exact in 32 bits
+            const uint32_t d = __vabsdiffu4(a, b);
+            return __dp4a(d, d, 0u);
         } else if constexpr (C == 1) {
             uint32_t d = 0;
 #pragma unroll
