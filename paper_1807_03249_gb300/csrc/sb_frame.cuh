@@ -929,9 +929,10 @@ __device__ __forceinline__ void frame_tile(const FrameArgs &a, int tile_x, int t
     }
 }
 
-// CTAs per SM the kernels are compiled for: wide windows (R >= 3) spend more
-// of each tile waiting on loads, so they trade registers (64) for a fourth CTA.
-__host__ __device__ constexpr int min_ctas(int R) { return R >= 3 ? 4 : 3; }
+// CTAs per SM the kernels are compiled for: four (64 registers a thread) hide
+// more of each tile's load latency than three with 80 registers; five (48)
+// spill too much.
+__host__ __device__ constexpr int min_ctas(int) { return 4; }
 
 template <int C, int B, int MODE, int R>
 __global__ void __launch_bounds__(kThreads, min_ctas(R)) frame_kernel(const FrameArgs a) {

@@ -107,7 +107,10 @@ def test_workload_256_every_radius(cuda_device, radius):
 @pytest.mark.parametrize("shape,levels,T,seed", [
     ((1, 1), 3, 100, 0), ((1, 97), 4, 50, 1), ((65, 1), 2, 50, 2), ((33, 65), 5, 0, 3),
     ((129, 70), 1, 100, 4), ((70, 129), 12, 200, 5), ((100, 190), 6, (1 << 64) - 1, 6),
-    ((64, 32), 7, 400, 0xFFFFFFFF), ((31, 200), 3, 300, 12345)])
+    ((64, 32), 7, 400, 0xFFFFFFFF), ((31, 200), 3, 300, 12345),
+    # level 8 (the largest level with packed seed keys) with every pixel falling
+    # to level 1, level 8 with a mid threshold, level 9 (per-pixel lists)
+    ((300, 520), 8, 0, 77), ((97, 203), 8, 2000, 79), ((260, 300), 9, 500, 78)])
 def test_ragged_and_extreme_parameters(cuda_device, shape, levels, T, seed):
     H, W = shape
     tgt = synth.smooth_integer_guide(seed % 1000 + 1, H, W, 3, step=5)
