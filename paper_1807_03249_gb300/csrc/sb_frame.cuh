@@ -47,8 +47,6 @@ constexpr int kTW = 64;
 constexpr int kTH = 32;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kBatch = 4;                   // pixels per thread per batch
-constexpr uint32_t kPending = 0xFFFFFFFEu;  // in-target pixel without an assignment yet
 constexpr int kEagerMinLevel = 3;           // levels >= this get their cells in phase 0
 constexpr int kKeyShift = 11;               // cell-index bits of the packed seed key
 constexpr int kPackedMaxLevel = 8;          // levels whose packed keys fit 32 bits
@@ -211,45 +209,6 @@ __device__ __forceinline__ void build_cells(const FrameArgs &a, int4 *cells, int
     }
 }
 
-// Nearest seed of region pixel (prx, pry) (region-centred) at level l: returns
-// the chosen cell; qneg = -q in region-centred coordinates.
-__device__ __forceinline__ int4 nearest_cell(const int4 *cells, int base, int c0, int ncy, int l,
-                                             int prx, int pry, int &qneg_x, int &qneg_y) {
-    if (l <= kPackedMaxLevel) {
-        int key = INT_MAX;
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-#pragma unroll
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int4 cl = cells[c0 + dx * ncy + dy];
-                key = min(key, cl.z + cl.x * prx + cl.y * pry);
-            }
-        }
-        const int4 cl = cells[base + (key & ((1 << kKeyShift) - 1))];
-        qneg_x = cl.x >> (kKeyShift + 1);
-        qneg_y = cl.y >> (kKeyShift + 1);
-        return cl;
-    }
-    int best_e = INT_MAX, best_c = c0;
-#pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int c = c0 + dx * ncy + dy;
-            const int4 cl = cells[c];
-            const int e = cl.z + cl.x * prx + cl.y * pry;
-            if (e < best_e) {
-                best_e = e;
-                best_c = c;
-            }
-        }
-    }
-    const int4 cl = cells[best_c];
-    qneg_x = cl.x >> 1;
-    qneg_y = cl.y >> 1;
-    return cl;
-}
-
 // Vertical segments of 4 pixels starting at target rows that are multiples of
 // 4 cover the region (the tile plus its R halo): segment s takes region column
 // s % RW, so the lanes of a warp hold neighbouring columns.  At every level
@@ -287,8 +246,15 @@ struct Segs {
 // ibase + j * RW and its candidate source position is (sx[j], sy[j]).
 // Accepted pixels get A (and the level); the bits of rejected pixels of m
 // are returned.
+// The source side of a candidate test.
+struct SrcView {
+    const uint32_t *src_packed;
+    int Ws, Hs;
+    uint64_t threshold;
+};
+
 template <int C, int B, int RW>
-__device__ __forceinline__ uint32_t test_segment(const FrameArgs &a, const uint32_t *gt,
+__device__ __forceinline__ uint32_t test_segment(const SrcView &a, const uint32_t *gt,
                                                  uint32_t *A, uint8_t *lev, int l, uint32_t t32,
                                                  uint32_t m, int ibase, const int (&sx)[4],
                                                  const int (&sy)[4]) {
@@ -320,7 +286,69 @@ __device__ __forceinline__ uint32_t test_segment(const FrameArgs &a, const uint3
     return rej;
 }
 
-// Level l (1 <= l <= kPackedMaxLevel) of the pixels m of the segment at
+// Levels where every pixel searches its own seed: level 1 (a segment spans
+// two cells) and the levels above kPackedMaxLevel (unscaled cells, 64-bit
+// keys).  Out of line: they are rare, and inlined they would crowd the
+// registers of the common path.
+template <int C, int B, int R>
+__device__ __noinline__ uint32_t segment_level_rare(SrcView a, const uint32_t *gt, uint32_t *A,
+                                                    uint8_t *lev, const int4 *cells, int base,
+                                                    int c0, int ncy, int l, uint32_t t32, int rx,
+                                                    int ry, uint32_t m) {
+    constexpr int RW = Segs<R>::RW, RH = Segs<R>::RH;
+    constexpr int kMask = (1 << kKeyShift) - 1;
+    const int prx = rx - RW / 2, pry = ry - RH / 2;
+    const int ibase = ry * RW + rx;
+    int sx[4], sy[4];
+    if (l > kPackedMaxLevel) {
+        // cells hold unscaled (-2q, |q|^2): the key (distance term, cell index)
+        // takes 64 bits; each pixel searches
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!((m >> j) & 1u)) continue;
+            long long key = LLONG_MAX;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+#pragma unroll
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int c = c0 + dx * ncy + dy;
+                    const int4 cl = cells[c];
+                    const int e = cl.z + cl.x * prx + cl.y * (pry + j);
+                    key = min(key, ((long long)e << kKeyShift) | (long long)(c - base));
+                }
+            }
+            const int4 cl = cells[base + (int)(key & kMask)];
+            sx[j] = (int)((uint32_t)cl.w & 0xFFFFu) + prx + (cl.x >> 1);
+            sy[j] = (int)((uint32_t)cl.w >> 16) + pry + j + (cl.y >> 1);
+        }
+        return test_segment<C, B, RW>(a, gt, A, lev, l, t32, m, ibase, sx, sy);
+    }
+    if (l == 1) {
+        // rows 0-1 and 2-3 lie in consecutive cells of one column
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!((m >> j) & 1u)) continue;
+            int key = INT_MAX;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+#pragma unroll
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int4 cl = cells[c0 + (j >> 1) + dx * ncy + dy];
+                    key = min(key, cl.z + cl.x * prx + cl.y * (pry + j));
+                }
+            }
+            const int4 cc = cells[base + (key & kMask)];
+            sx[j] = (int)((uint32_t)cc.w & 0xFFFFu) + prx + (cc.x >> (kKeyShift + 1));
+            sy[j] = (int)((uint32_t)cc.w >> 16) + pry + j + (cc.y >> (kKeyShift + 1));
+            const int x = min(max(sx[j], 0), a.Ws - 1), y = min(max(sy[j], 0), a.Hs - 1);
+            A[ibase + j * RW] = (uint32_t)x | ((uint32_t)y << 16);
+            if (lev) lev[ibase + j * RW] = 1;
+        }
+    }
+    return 0;  // level 1 accepts every pixel
+}
+
+// Level l (1 <= l <= kMaxLevels) of the pixels m of the segment at
 // region (rx, ry): returns the rejected ones.  The packed keys of the nine
 // candidates are affine in p, so the pixels that pick a given seed form a
 // convex set: when the first and last pixel of m pick the same seed, every
@@ -344,27 +372,10 @@ __device__ __forceinline__ uint32_t segment_level(const FrameArgs &a, const uint
         sx[j] = (int)((uint32_t)cl.w & 0xFFFFu) + prx + (cl.x >> (kKeyShift + 1));
         sy[j] = (int)((uint32_t)cl.w >> 16) + pry + j + (cl.y >> (kKeyShift + 1));
     };
-    if (l == 1) {
-        // rows 0-1 and 2-3 lie in consecutive cells of one column
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (!((m >> j) & 1u)) continue;
-            int key = INT_MAX;
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-#pragma unroll
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const int4 cl = cells[c0 + (j >> 1) + dx * g.ncy + dy];
-                    key = min(key, cl.z + cl.x * prx + cl.y * (pry + j));
-                }
-            }
-            candidate(j, key);
-            const int x = min(max(sx[j], 0), a.Ws - 1), y = min(max(sy[j], 0), a.Hs - 1);
-            A[ibase + j * RW] = (uint32_t)x | ((uint32_t)y << 16);
-            if (lev) lev[ibase + j * RW] = 1;
-        }
-        return 0;
-    }
+    const SrcView sv{a.src_packed, a.Ws, a.Hs, a.threshold};
+    if (l == 1 || l > kPackedMaxLevel)
+        return segment_level_rare<C, B, R>(sv, gt, A, lev, cells, base, c0, g.ncy, l, t32, rx, ry,
+                                           m);
     const int jlo = __ffs(m) - 1, jhi = 31 - __clz(m);
     int klo = INT_MAX, khi = INT_MAX;
 #pragma unroll
@@ -399,7 +410,7 @@ __device__ __forceinline__ uint32_t segment_level(const FrameArgs &a, const uint
 #pragma unroll
         for (int j = 0; j < 4; ++j) candidate(j, k[j]);
     }
-    return test_segment<C, B, RW>(a, gt, A, lev, l, t32, m, ibase, sx, sy);
+    return test_segment<C, B, RW>(sv, gt, A, lev, l, t32, m, ibase, sx, sy);
 }
 
 // One level over segments: the top level visits every segment of the region
@@ -443,7 +454,7 @@ template <int C, int B, int R>
 __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayout &L, int rx0,
                                               int ry0, unsigned char *smem, uint8_t *lev) {
     using F = GuideFmt<C, B>;
-    constexpr int RW = kTW + 2 * R, RH = kTH + 2 * R, NR = RW * RH;
+    constexpr int RW = kTW + 2 * R, RH = kTH + 2 * R;
     int4 *cells = reinterpret_cast<int4 *>(smem + L.off_cells);
     uint32_t *gt = reinterpret_cast<uint32_t *>(smem + L.off_gt);
     uint32_t *A = reinterpret_cast<uint32_t *>(smem + L.off_A);
@@ -459,9 +470,6 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     const int L_top = a.levels;
     const int eager_lo = L_top <= kEagerMinLevel ? 1 : kEagerMinLevel;
 
-    // with 2 <= L <= kPackedMaxLevel every level goes by segments (the lists
-    // hold segments with pending pixels); otherwise by lists of pixels
-    const bool seg_mode = L_top >= 2 && L_top <= kPackedMaxLevel;
     if (tid == 0) {
         cnt[0] = 0;
         cnt[1] = 0;
@@ -501,56 +509,26 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
         for (int j = 0; j < 4; ++j) {
             if (!((rl >> j) & 1u)) continue;
             const int i = (ry + j) * RW + rx;
-            if ((it >> j) & 1u) {
-                gt[i] = gv[q][j];
-                if (!seg_mode) A[i] = kPending;
-            } else {
-                A[i] = kInvalid;
-            }
+            if ((it >> j) & 1u) gt[i] = gv[q][j];
+            else A[i] = kInvalid;
         }
     }
     if (has_cell) cells[tid] = cell_value(ct, cu, cxo, cyo);
     build_cells<C, B>(a, cells, L_top, eager_lo, 0, xa, xb, ya, yb, cxo, cyo, kThreads);
     __syncthreads();
 
-    if (seg_mode) {
-        int n_pend, base, cur = 1;
-        {
-            // top level over every segment (cells of the top level start at 0)
-            const LevelCells g = level_cells(L_top, xa, xb, ya, yb);
-            level_segments<C, B, R, true>(a, gt, A, lev, cells, 0, g, L_top, rx0, ry0, t32,
-                                          nullptr, 0, list1, &cnt[1]);
-            __syncthreads();
-            n_pend = cnt[1];
-            base = g.ncx * g.ncy;
-            __syncthreads();  // every thread has read cnt[1] before the next level writes cnt[0]
-        }
-        for (int l = L_top - 1; l >= 1 && n_pend > 0; --l) {
-            const LevelCells g = level_cells(l, xa, xb, ya, yb);
-            if (l == kEagerMinLevel - 1 && eager_lo > 1) {
-                // a pixel still needs the fine levels: build levels 2 and 1 now
-                build_cells<C, B>(a, cells, l, 1, base, xa, xb, ya, yb, cxo, cyo);
-                __syncthreads();
-            }
-            const int nxt = cur ^ 1;
-            level_segments<C, B, R, false>(a, gt, A, lev, cells, base, g, l, rx0, ry0, t32,
-                                           cur ? list1 : list0, n_pend, cur ? list0 : list1,
-                                           &cnt[nxt]);
-            __syncthreads();
-            n_pend = cnt[nxt];
-            if (tid == 0) cnt[cur] = 0;  // see the pixel-list loop below
-            base += g.ncx * g.ncy;
-            __syncthreads();
-            cur = nxt;
-        }
-        return;
+    int n_pend, base, cur = 1;
+    {
+        // top level over every segment (cells of the top level start at 0)
+        const LevelCells g = level_cells(L_top, xa, xb, ya, yb);
+        level_segments<C, B, R, true>(a, gt, A, lev, cells, 0, g, L_top, rx0, ry0, t32,
+                                      nullptr, 0, list1, &cnt[1]);
+        __syncthreads();
+        n_pend = cnt[1];
+        base = g.ncx * g.ncy;
+        __syncthreads();  // every thread has read cnt[1] before the next level writes cnt[0]
     }
-
-    int cur = 0;
-    int n_pend = NR;  // the top level scans the whole region
-    int base = 0;     // first cell of the current level
-    const int l_start = L_top;
-    for (int l = l_start; l >= 1 && n_pend > 0; --l) {
+    for (int l = L_top - 1; l >= 1 && n_pend > 0; --l) {
         const LevelCells g = level_cells(l, xa, xb, ya, yb);
         if (l == kEagerMinLevel - 1 && eager_lo > 1) {
             // a pixel still needs the fine levels: build levels 2 and 1 now
@@ -558,66 +536,9 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
             __syncthreads();
         }
         const int nxt = cur ^ 1;
-        const uint16_t *list_cur = cur ? list1 : list0;
-        uint16_t *list_nxt = cur ? list0 : list1;
-        const bool top = l == L_top;
-        for (int j0 = 0; j0 < n_pend; j0 += kThreads * kBatch) {
-            int idx[kBatch];
-            uint32_t sv[kBatch], gsv[kBatch];
-            bool act[kBatch], inb[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int j = j0 + u * kThreads + tid;
-                act[u] = j < n_pend;
-                int i = 0;
-                if (act[u]) {
-                    i = top ? j : list_cur[j];
-                    if (top) act[u] = A[i] == kPending;
-                }
-                idx[u] = i;
-                inb[u] = false;
-                gsv[u] = 0;
-                sv[u] = 0;
-                if (act[u]) {
-                    const int rx = i % RW, ry = i / RW;
-                    const int prx = rx - RW / 2, pry = ry - RH / 2;
-                    const int lcx = ((rx0 + rx) >> l) - g.cx0, lcy = ((ry0 + ry) >> l) - g.cy0;
-                    int qnx, qny;
-                    const int4 cl = nearest_cell(cells, base, base + lcx * g.ncy + lcy, g.ncy, l,
-                                                 prx, pry, qnx, qny);
-                    int sx = (int)((uint32_t)cl.w & 0xFFFFu) + prx + qnx;
-                    int sy = (int)((uint32_t)cl.w >> 16) + pry + qny;
-                    if (l > 1) {
-                        inb[u] = (unsigned)sx < (unsigned)a.Ws && (unsigned)sy < (unsigned)a.Hs;
-                        if (inb[u]) gsv[u] = __ldg(a.src_packed + (int64_t)sy * a.Ws + sx);
-                    } else {
-                        sx = min(max(sx, 0), a.Ws - 1);
-                        sy = min(max(sy, 0), a.Hs - 1);
-                    }
-                    sv[u] = (uint32_t)sx | ((uint32_t)sy << 16);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                bool acc = false;
-                if (act[u]) {
-                    if (l > 1) {
-                        if (inb[u]) {
-                            const uint64_t d = F::dist(gsv[u], gt[idx[u]]);
-                            if constexpr (B == 8) acc = (uint32_t)d <= t32;
-                            else acc = d <= a.threshold;
-                        }
-                    } else {
-                        acc = true;
-                    }
-                    if (acc) {
-                        A[idx[u]] = sv[u];
-                        if (lev) lev[idx[u]] = (uint8_t)l;
-                    }
-                }
-                list_push(act[u] && !acc, idx[u], list_nxt, &cnt[nxt]);
-            }
-        }
+        level_segments<C, B, R, false>(a, gt, A, lev, cells, base, g, l, rx0, ry0, t32,
+                                       cur ? list1 : list0, n_pend, cur ? list0 : list1,
+                                       &cnt[nxt]);
         __syncthreads();
         n_pend = cnt[nxt];
         // cnt[cur] was last read before the barrier above; it becomes the next
