@@ -80,7 +80,7 @@ typedef struct {
     const uint8_t *data;
     int32_t width;
     int32_t height;
-    int64_t row_stride;        /* bytes, multiple of 4, >= 4*width */
+    int64_t row_stride;        /* bytes, multiple of 4, >= 4*width; height*row_stride < 2^33 */
 } sb_rgba8;
 
 /* Opaque, library-owned guide look-up table of one exemplar. */

@@ -1,5 +1,6 @@
 // Host-side argument validation, status strings and error plumbing of the
 // StyleBlit C ABI.
+#include <cstdint>
 #include <cstdio>
 #include <string>
 
@@ -100,6 +101,11 @@ sb_status check_style(const sb_rgba8 *s, const char *name) {
     if (s->row_stride < 4LL * s->width || (s->row_stride % 4) != 0 ||
         ((uintptr_t)s->data % 4) != 0) {
         std::snprintf(buf, sizeof buf, "%s: row_stride must be >= 4*width and data/stride 4-byte aligned", name);
+        return fail(SB_ERR_INVALID_ARG, buf);
+    }
+    // the kernels address the style with 32-bit pixel offsets
+    if ((int64_t)s->height * (s->row_stride / 4) > INT32_MAX) {
+        std::snprintf(buf, sizeof buf, "%s: height * row_stride must stay below 2^33 bytes", name);
         return fail(SB_ERR_INVALID_ARG, buf);
     }
     return SB_OK;

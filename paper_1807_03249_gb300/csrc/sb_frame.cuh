@@ -63,7 +63,7 @@ struct FrameArgs {
     int key_bits;
     int key_channels;
     const uint8_t *style;
-    int64_t style_stride;
+    int style_stride_px;         // style row stride in pixels (height * stride < 2^31)
     int levels;
     uint64_t threshold;
     uint32_t seed;
@@ -168,7 +168,11 @@ __device__ __forceinline__ CellTask cell_task(const FrameArgs &a, int k, int l_h
         g = level_cells(l, xa, xb, ya, yb);
     }
     const int ci = k - off;  // column-major: ci = lcx * ncy + lcy
-    const int lcx = ci / g.ncy, lcy = ci - lcx * g.ncy;
+    // ci / ncy through a float reciprocal: ci < 2^11 and ncy < 2^6 keep the
+    // true quotient at least 0.5 / ncy from an integer, far above the
+    // rounding error, so the truncation is exact
+    const int lcx = (int)(((float)ci + 0.5f) * __frcp_rn((float)g.ncy));
+    const int lcy = ci - lcx * g.ncy;
     const int h = 1 << l;
     const int bx = g.cx0 + lcx, by = g.cy0 + lcy;
     const uint32_t hsh = cell_hash(level_key(a.seed, l), bx, by);
@@ -265,7 +269,8 @@ __device__ __forceinline__ uint32_t test_segment(const SrcView &a, const uint32_
     for (int j = 0; j < 4; ++j) {
         ok[j] = ((m >> j) & 1u) && (unsigned)sx[j] < (unsigned)a.Ws &&
                 (unsigned)sy[j] < (unsigned)a.Hs;
-        gsv[j] = ok[j] ? __ldg(a.src_packed + (int64_t)sy[j] * a.Ws + sx[j]) : 0u;
+        gsv[j] = ok[j] ? __ldg(a.src_packed + ((uint32_t)sy[j] * (uint32_t)a.Ws + (uint32_t)sx[j]))
+                       : 0u;
     }
     uint32_t rej = 0;
 #pragma unroll
@@ -486,12 +491,13 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
         cg = F::load(a.tgt, a.tgt_stride, ct.sx, ct.sy);
     }
     constexpr int kSegIters = (Segs<R>::NS + kThreads - 1) / kThreads;
-    uint32_t gv[kSegIters][4];
+    uint32_t gv[kSegIters][4], itq[kSegIters];
 #pragma unroll
     for (int q = 0; q < kSegIters; ++q) {
         const int sg = q * kThreads + tid;
         const int rx = Segs<R>::rx(sg), ry = Segs<R>::ry(sg);
         const uint32_t it = sg < Segs<R>::NS ? Segs<R>::mask(rx, ry, rx0, ry0, a.W, a.H) : 0u;
+        itq[q] = it;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             gv[q][j] = ((it >> j) & 1u) ? F::load(a.tgt, a.tgt_stride, rx0 + rx, ry0 + ry + j) : 0u;
@@ -504,12 +510,11 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
         if (sg >= Segs<R>::NS) continue;
         const int rx = Segs<R>::rx(sg), ry = Segs<R>::ry(sg);
         const uint32_t rl = Segs<R>::rows(ry);
-        const uint32_t it = Segs<R>::mask(rx, ry, rx0, ry0, a.W, a.H);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (!((rl >> j) & 1u)) continue;
             const int i = (ry + j) * RW + rx;
-            if ((it >> j) & 1u) gt[i] = gv[q][j];
+            if ((itq[q] >> j) & 1u) gt[i] = gv[q][j];
             else A[i] = kInvalid;
         }
     }
@@ -610,7 +615,7 @@ __device__ __forceinline__ uint32_t div_round(uint32_t s, uint32_t n, uint32_t m
     return n == 1 ? y : __umulhi(y, m);
 }
 
-template <bool F32, typename Acc>
+template <bool F32, int R, typename Acc>
 __device__ __forceinline__ void vote_store(const FrameArgs &a, const Acc &acc, int gx, int gy) {
     uint32_t s0, s1, s2, s3;
     acc.sums(s0, s1, s2, s3);
@@ -626,7 +631,9 @@ __device__ __forceinline__ void vote_store(const FrameArgs &a, const Acc &acc, i
     } else {
         uint32_t o = 0;
         if (n) {
-            const uint32_t m = 0xFFFFFFFFu / n + 1u;
+            // a full window (the common case) divides by a constant
+            constexpr uint32_t kFull = (2 * R + 1) * (2 * R + 1);
+            const uint32_t m = n == kFull ? 0xFFFFFFFFu / kFull + 1u : 0xFFFFFFFFu / n + 1u;
             o = div_round(s0, n, m) | (div_round(s1, n, m) << 8) | (div_round(s2, n, m) << 16) |
                 (div_round(s3, n, m) << 24);
         }
@@ -652,7 +659,7 @@ __device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const uint32_
     constexpr bool kPacked = (2 * R + 1) * (2 * R + 1) * 255 < 65536;
     constexpr uint32_t kBreakMask = (2 * R >= 32) ? 0xFFFFFFFFu : ((1u << (2 * R)) - 1u);
     const uint32_t *style32 = reinterpret_cast<const uint32_t *>(a.style);
-    const int64_t sstride = a.style_stride >> 2;
+    const int sstride = a.style_stride_px;
     auto tap = [&](VoteAcc<kPacked> &acc, const uint32_t *row, int tx, int col, int oy,
                    uint32_t len) {
         const uint32_t c = row[col];
@@ -660,7 +667,7 @@ __device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const uint32_
         const uint32_t vx = v & 0xFFFFu, vy = v >> 16;
         // an out-of-target tap (kInvalid) lands out of the source here
         const bool ok = len != 0u && vx < (uint32_t)a.Ws && vy < (uint32_t)a.Hs;
-        const uint32_t colr = ok ? __ldg(style32 + (int64_t)vy * sstride + vx) : 0u;
+        const uint32_t colr = ok ? __ldg(style32 + (vy * (uint32_t)sstride + vx)) : 0u;
         acc.add(colr, ok ? len : 0u);
     };
     if (threadIdx.x == 0) *cplx_cnt = 0;
@@ -687,7 +694,7 @@ __device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const uint32_
                 tap(acc, row, tx, min(tx + j1 + 1, tx + 2 * R), oy,
                     pc == 1 ? (uint32_t)(2 * R - j1) : 0u);
             }
-            if (!complex_row) vote_store<F32>(a, acc, x0 + tx, y0 + ty);
+            if (!complex_row) vote_store<F32, R>(a, acc, x0 + tx, y0 + ty);
         }
         list_push(act && complex_row, k, cplx, cplx_cnt);
     }
@@ -702,7 +709,7 @@ __device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const uint32_
 #pragma unroll
             for (int ox = 0; ox <= 2 * R; ++ox) tap(acc, row, tx, tx + ox, oy, 1u);
         }
-        vote_store<F32>(a, acc, x0 + tx, y0 + ty);
+        vote_store<F32, R>(a, acc, x0 + tx, y0 + ty);
     }
 }
 
@@ -722,7 +729,7 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
     uint16_t *slow = reinterpret_cast<uint16_t *>(smem + L.off_list0);
     int *slow_cnt = reinterpret_cast<int *>(smem + L.off_cnt) + 2;
     const uint32_t *style32 = reinterpret_cast<const uint32_t *>(a.style);
-    const int64_t sstride = a.style_stride >> 2;
+    const int sstride = a.style_stride_px;
 
     if (threadIdx.x == 0) *slow_cnt = 0;
     if constexpr (R > 0) {
@@ -796,7 +803,7 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
                 const bool ok = ((U >> tx) & 1ull) && cx < a.Ws && cy < a.Hs;
                 uni[q][c] = ok;
                 need[q][c] = !ok;
-                if (ok) col[q][c] = __ldg(style32 + (int64_t)cy * sstride + cx);
+                if (ok) col[q][c] = __ldg(style32 + ((uint32_t)cy * (uint32_t)sstride + (uint32_t)cx));
             }
         }
     }
@@ -825,9 +832,8 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
 
 // One 64 x 32 output tile (tile_x, tile_y) of one frame.
 template <int C, int B, int MODE, int R>
-__device__ __forceinline__ void frame_tile(const FrameArgs &a, int tile_x, int tile_y,
-                                           unsigned char *smem) {
-    const SmemLayout L = smem_layout(R, a.levels);
+__device__ __forceinline__ void frame_tile(const FrameArgs &a, const SmemLayout &L, int tile_x,
+                                           int tile_y, unsigned char *smem) {
     const int x0 = tile_x * kTW, y0 = tile_y * kTH;
     uint8_t *bytes = smem + L.off_bytes;
     assign_region<C, B, R>(a, L, x0 - R, y0 - R, smem, MODE == kAssign ? bytes : nullptr);
@@ -856,9 +862,10 @@ __device__ __forceinline__ void frame_tile(const FrameArgs &a, int tile_x, int t
 __host__ __device__ constexpr int min_ctas(int) { return 4; }
 
 template <int C, int B, int MODE, int R>
-__global__ void __launch_bounds__(kThreads, min_ctas(R)) frame_kernel(const FrameArgs a) {
+__global__ void __launch_bounds__(kThreads, min_ctas(R))
+    frame_kernel(const FrameArgs a, const SmemLayout L) {
     extern __shared__ __align__(16) unsigned char smem[];
-    frame_tile<C, B, MODE, R>(a, blockIdx.x, blockIdx.y, smem);
+    frame_tile<C, B, MODE, R>(a, L, blockIdx.x, blockIdx.y, smem);
 }
 
 // Many frames in one launch: block b stylises tile b - tile_start[k] of the
@@ -876,7 +883,8 @@ struct BatchArgs {
 };
 
 template <int C, int B, int R>
-__global__ void __launch_bounds__(kThreads, min_ctas(R)) batch_kernel(const __grid_constant__ BatchArgs b) {
+__global__ void __launch_bounds__(kThreads, min_ctas(R))
+    batch_kernel(const __grid_constant__ BatchArgs b, const SmemLayout L) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int t = (int)blockIdx.x;
     int lo = 0, hi = b.n - 1;  // last frame whose first tile is <= t
@@ -887,7 +895,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas(R)) batch_kernel(const __gr
     }
     const FrameArgs a = b.f[lo];  // register copy: field reads become plain operands
     const int lt = t - b.tile_start[lo];
-    frame_tile<C, B, kStylize, R>(a, lt % b.tiles_x[lo], lt / b.tiles_x[lo], smem);
+    frame_tile<C, B, kStylize, R>(a, L, lt % b.tiles_x[lo], lt / b.tiles_x[lo], smem);
 }
 
 template <bool F32, int R>
@@ -929,27 +937,28 @@ cudaError_t ensure_smem(size_t smem) {
     return e;
 }
 
-template <auto Kernel>
-cudaError_t launch_tiles(size_t smem, int W, int H, cudaStream_t s, const FrameArgs &a) {
+template <auto Kernel, typename... Args>
+cudaError_t launch_tiles(size_t smem, int W, int H, cudaStream_t s, const Args &...args) {
     cudaError_t e = ensure_smem<Kernel>(smem);
     if (e != cudaSuccess) return e;
     dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
-    Kernel<<<grid, kThreads, smem, s>>>(a);
+    Kernel<<<grid, kThreads, smem, s>>>(args...);
     return cudaGetLastError();
 }
 
 template <int C, int B, int R>
 cudaError_t launch_stylize_r(const FrameArgs &a, cudaStream_t s) {
-    return launch_tiles<frame_kernel<C, B, kStylize, R>>(smem_layout(R, a.levels).total, a.W,
-                                                        a.H, s, a);
+    const SmemLayout L = smem_layout(R, a.levels);
+    return launch_tiles<frame_kernel<C, B, kStylize, R>>(L.total, a.W, a.H, s, a, L);
 }
 
 template <int C, int B, int R>
 cudaError_t launch_batch_r(const BatchArgs &b, int max_levels, cudaStream_t s) {
-    const size_t smem = smem_layout(R, max_levels).total;
-    cudaError_t e = ensure_smem<batch_kernel<C, B, R>>(smem);
+    // one layout (for the deepest frame) serves every tile of the launch
+    const SmemLayout L = smem_layout(R, max_levels);
+    cudaError_t e = ensure_smem<batch_kernel<C, B, R>>(L.total);
     if (e != cudaSuccess) return e;
-    batch_kernel<C, B, R><<<b.tile_start[b.n], kThreads, smem, s>>>(b);
+    batch_kernel<C, B, R><<<b.tile_start[b.n], kThreads, L.total, s>>>(b, L);
     return cudaGetLastError();
 }
 
@@ -972,9 +981,10 @@ cudaError_t launch_batch(const BatchArgs &b, int r, int max_levels, cudaStream_t
 // Launches the frame kernel of guide format <C, B> in the given mode.
 template <int C, int B>
 cudaError_t launch_frame(int mode, const FrameArgs &a, cudaStream_t s) {
-    if (mode == kAssign)
-        return launch_tiles<frame_kernel<C, B, kAssign, 0>>(smem_layout(0, a.levels).total, a.W,
-                                                            a.H, s, a);
+    if (mode == kAssign) {
+        const SmemLayout L = smem_layout(0, a.levels);
+        return launch_tiles<frame_kernel<C, B, kAssign, 0>>(L.total, a.W, a.H, s, a, L);
+    }
     switch (a.radius) {
         case 0: return launch_stylize_r<C, B, 0>(a, s);
         case 1: return launch_stylize_r<C, B, 1>(a, s);

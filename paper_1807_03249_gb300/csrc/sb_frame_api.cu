@@ -152,7 +152,7 @@ extern "C" sb_status sb_stylize(const sb_guide *tgt_guide, const sb_guide *src_g
         return fail(SB_ERR_INVALID_ARG, "rgba8_out: NULL or not 4-byte aligned");
     FrameArgs a = frame_args(tgt_guide, lut, levels, threshold, seed);
     a.style = src_style->data;
-    a.style_stride = src_style->row_stride;
+    a.style_stride_px = (int)(src_style->row_stride / 4);
     a.radius = blend_radius;
     a.rgba_out = reinterpret_cast<uint32_t *>(rgba8_out);
     cudaError_t e = launch_frame_any(tgt_guide->channels, tgt_guide->bits, kStylize, a,
@@ -187,7 +187,7 @@ extern "C" sb_status sb_blend(const uint32_t *assign, int32_t tgt_w, int32_t tgt
     a.Ws = src_style->width;
     a.Hs = src_style->height;
     a.style = src_style->data;
-    a.style_stride = src_style->row_stride;
+    a.style_stride_px = (int)(src_style->row_stride / 4);
     a.radius = blend_radius;
     a.assign_in = assign;
     a.rgba_out = reinterpret_cast<uint32_t *>(rgba8_out);
@@ -239,7 +239,7 @@ extern "C" sb_status sb_stylize_batch(const sb_frame *frames, int32_t n_frames,
         b.tiles_x[k] = tx > 0 ? tx : 1;
         FrameArgs a = frame_args(&f.tgt_guide, f.lut, f.levels, f.threshold, f.seed);
         a.style = f.src_style.data;
-        a.style_stride = f.src_style.row_stride;
+        a.style_stride_px = (int)(f.src_style.row_stride / 4);
         a.radius = blend_radius;
         a.rgba_out = reinterpret_cast<uint32_t *>(f.rgba8_out);
         b.f[k] = a;
