@@ -293,64 +293,60 @@ __device__ __forceinline__ uint32_t test_segment(const SrcView &a, const uint32_
 
 // Levels where every pixel searches its own seed: level 1 (a segment spans
 // two cells) and the levels above kPackedMaxLevel (unscaled cells, 64-bit
-// keys).  Out of line: they are rare, and inlined they would crowd the
-// registers of the common path.
+// keys).  Both are rare, so pixels go one at a time with little live state
+// (the common path keeps its registers).
 template <int C, int B, int R>
-__device__ __noinline__ uint32_t segment_level_rare(SrcView a, const uint32_t *gt, uint32_t *A,
-                                                    uint8_t *lev, const int4 *cells, int base,
-                                                    int c0, int ncy, int l, uint32_t t32, int rx,
-                                                    int ry, uint32_t m) {
+__device__ __forceinline__ uint32_t segment_level_rare(const SrcView &a, const uint32_t *gt,
+                                                       uint32_t *A, uint8_t *lev,
+                                                       const int4 *cells, int base, int c0,
+                                                       int ncy, int l, uint32_t t32, int rx,
+                                                       int ry, uint32_t m) {
+    using F = GuideFmt<C, B>;
     constexpr int RW = Segs<R>::RW, RH = Segs<R>::RH;
     constexpr int kMask = (1 << kKeyShift) - 1;
     const int prx = rx - RW / 2, pry = ry - RH / 2;
-    const int ibase = ry * RW + rx;
-    int sx[4], sy[4];
-    if (l > kPackedMaxLevel) {
-        // cells hold unscaled (-2q, |q|^2): the key (distance term, cell index)
-        // takes 64 bits; each pixel searches
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (!((m >> j) & 1u)) continue;
-            long long key = LLONG_MAX;
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-#pragma unroll
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const int c = c0 + dx * ncy + dy;
-                    const int4 cl = cells[c];
-                    const int e = cl.z + cl.x * prx + cl.y * (pry + j);
-                    key = min(key, ((long long)e << kKeyShift) | (long long)(c - base));
-                }
-            }
-            const int4 cl = cells[base + (int)(key & kMask)];
-            sx[j] = (int)((uint32_t)cl.w & 0xFFFFu) + prx + (cl.x >> 1);
-            sy[j] = (int)((uint32_t)cl.w >> 16) + pry + j + (cl.y >> 1);
+    const bool packed = l <= kPackedMaxLevel;
+    uint32_t rej = 0;
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+        if (!((m >> j) & 1u)) continue;
+        // level 1: rows 0-1 and 2-3 lie in consecutive cells of one column
+        const int cj = c0 + (l == 1 ? (j >> 1) : 0);
+        long long key = LLONG_MAX;
+#pragma unroll 1
+        for (int d = 0; d < 9; ++d) {
+            const int c = cj + (d / 3 - 1) * ncy + (d % 3 - 1);
+            const int4 cl = cells[c];
+            const int e = cl.z + cl.x * prx + cl.y * (pry + j);
+            // packed cells carry the index in their low bits already
+            key = min(key, packed ? (long long)e : (((long long)e << kKeyShift) | (c - base)));
         }
-        return test_segment<C, B, RW>(a, gt, A, lev, l, t32, m, ibase, sx, sy);
-    }
-    if (l == 1) {
-        // rows 0-1 and 2-3 lie in consecutive cells of one column
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (!((m >> j) & 1u)) continue;
-            int key = INT_MAX;
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-#pragma unroll
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const int4 cl = cells[c0 + (j >> 1) + dx * ncy + dy];
-                    key = min(key, cl.z + cl.x * prx + cl.y * (pry + j));
-                }
+        const int4 cl = cells[base + (int)(key & kMask)];
+        const int sh = packed ? kKeyShift + 1 : 1;
+        int sx = (int)((uint32_t)cl.w & 0xFFFFu) + prx + (cl.x >> sh);
+        int sy = (int)((uint32_t)cl.w >> 16) + pry + j + (cl.y >> sh);
+        const int i = (ry + j) * RW + rx;
+        bool acc = true;
+        if (l == 1) {
+            sx = min(max(sx, 0), a.Ws - 1);
+            sy = min(max(sy, 0), a.Hs - 1);
+        } else {
+            acc = (unsigned)sx < (unsigned)a.Ws && (unsigned)sy < (unsigned)a.Hs;
+            if (acc) {
+                const uint64_t d = F::dist(
+                    __ldg(a.src_packed + ((uint32_t)sy * (uint32_t)a.Ws + (uint32_t)sx)), gt[i]);
+                if constexpr (B == 8) acc = (uint32_t)d <= t32;
+                else acc = d <= a.threshold;
             }
-            const int4 cc = cells[base + (key & kMask)];
-            sx[j] = (int)((uint32_t)cc.w & 0xFFFFu) + prx + (cc.x >> (kKeyShift + 1));
-            sy[j] = (int)((uint32_t)cc.w >> 16) + pry + j + (cc.y >> (kKeyShift + 1));
-            const int x = min(max(sx[j], 0), a.Ws - 1), y = min(max(sy[j], 0), a.Hs - 1);
-            A[ibase + j * RW] = (uint32_t)x | ((uint32_t)y << 16);
-            if (lev) lev[ibase + j * RW] = 1;
+        }
+        if (acc) {
+            A[i] = (uint32_t)sx | ((uint32_t)sy << 16);
+            if (lev) lev[i] = (uint8_t)l;
+        } else {
+            rej |= 1u << j;
         }
     }
-    return 0;  // level 1 accepts every pixel
+    return rej;
 }
 
 // Level l (1 <= l <= kMaxLevels) of the pixels m of the segment at
