@@ -109,7 +109,7 @@ __host__ __device__ inline SmemLayout smem_layout(int r, int levels) {
     o += (size_t)s.NR;
     o = (o + 15) & ~(size_t)15;
     s.off_cnt = o;
-    o += 16;
+    o += 32;  // 3 level counters (rotating), slow and complex vote counters
     s.total = o;
     return s;
 }
@@ -518,37 +518,37 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     build_cells<C, B>(a, cells, L_top, eager_lo, 0, xa, xb, ya, yb, cxo, cyo, kThreads);
     __syncthreads();
 
-    int n_pend, base, cur = 1;
+    // level step t (0 = top) appends to counter t % 3; the counter of step
+    // t + 1 is cleared during step t (its last reader passed step t - 1's
+    // barrier), so one barrier per level publishes both the list and the reset
+    int n_pend, base;
     {
         // top level over every segment (cells of the top level start at 0)
         const LevelCells g = level_cells(L_top, xa, xb, ya, yb);
         level_segments<C, B, R, true>(a, gt, A, lev, cells, 0, g, L_top, rx0, ry0, t32,
-                                      nullptr, 0, list1, &cnt[1]);
+                                      nullptr, 0, list1, &cnt[0]);
         __syncthreads();
-        n_pend = cnt[1];
+        n_pend = cnt[0];
         base = g.ncx * g.ncy;
-        __syncthreads();  // every thread has read cnt[1] before the next level writes cnt[0]
     }
-    for (int l = L_top - 1; l >= 1 && n_pend > 0; --l) {
+    const uint16_t *list_cur = list1;
+    uint16_t *list_nxt = list0;
+    for (int l = L_top - 1, t = 1; l >= 1 && n_pend > 0; --l, ++t) {
         const LevelCells g = level_cells(l, xa, xb, ya, yb);
         if (l == kEagerMinLevel - 1 && eager_lo > 1) {
             // a pixel still needs the fine levels: build levels 2 and 1 now
             build_cells<C, B>(a, cells, l, 1, base, xa, xb, ya, yb, cxo, cyo);
             __syncthreads();
         }
-        const int nxt = cur ^ 1;
-        level_segments<C, B, R, false>(a, gt, A, lev, cells, base, g, l, rx0, ry0, t32,
-                                       cur ? list1 : list0, n_pend, cur ? list0 : list1,
-                                       &cnt[nxt]);
+        if (tid == 0) cnt[(t + 1) % 3] = 0;
+        level_segments<C, B, R, false>(a, gt, A, lev, cells, base, g, l, rx0, ry0, t32, list_cur,
+                                       n_pend, list_nxt, &cnt[t % 3]);
         __syncthreads();
-        n_pend = cnt[nxt];
-        // cnt[cur] was last read before the barrier above; it becomes the next
-        // level's output counter, and the barrier below publishes the reset
-        // before any thread appends to it
-        if (tid == 0) cnt[cur] = 0;
+        n_pend = cnt[t % 3];
         base += g.ncx * g.ncy;
-        __syncthreads();
-        cur = nxt;
+        const uint16_t *tmp = list_cur;
+        list_cur = list_nxt;
+        list_nxt = const_cast<uint16_t *>(tmp);
     }
 }
 
@@ -666,8 +666,6 @@ __device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const uint32_
         const uint32_t colr = ok ? __ldg(style32 + (vy * (uint32_t)sstride + vx)) : 0u;
         acc.add(colr, ok ? len : 0u);
     };
-    if (threadIdx.x == 0) *cplx_cnt = 0;
-    __syncthreads();
     for (int j0 = 0; j0 < n_slow; j0 += kThreads) {
         const int j = j0 + threadIdx.x;
         const bool act = j < n_slow;
@@ -723,11 +721,11 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
     uint64_t *v_row = hu_row + RH;
     uint32_t *E_row = reinterpret_cast<uint32_t *>(v_row + RH);  // 4 words per region row
     uint16_t *slow = reinterpret_cast<uint16_t *>(smem + L.off_list0);
-    int *slow_cnt = reinterpret_cast<int *>(smem + L.off_cnt) + 2;
+    int *slow_cnt = reinterpret_cast<int *>(smem + L.off_cnt) + 3;  // and the complex count
     const uint32_t *style32 = reinterpret_cast<const uint32_t *>(a.style);
     const int sstride = a.style_stride_px;
 
-    if (threadIdx.x == 0) *slow_cnt = 0;
+    if (threadIdx.x < 2) slow_cnt[threadIdx.x] = 0;
     if constexpr (R > 0) {
         // per region row: E bit x <=> A[x] == A[x-1] + 1 (both valid);
         // hu bit tx <=> E bits tx+1 .. tx+2R all set (columns tx..tx+2R form
