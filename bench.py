@@ -499,7 +499,8 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": "batch_kernel<3,8,2> (sb_stylize_batch)",
+                         "kernel": f"batch_kernel<{ex.guide.shape[2]},{ex.guide.dtype.itemsize * 8},"
+                                   f"{w.blend_radius}> (sb_stylize_batch)",
                          "peak_source": f"{peak_src} copy bandwidth",
                          "algorithmic_bytes_per_launch": alg,
                          "frame_only_frac": FRAMES_PER_STEP * ab["frame_bytes"] / kernel_s

@@ -201,9 +201,9 @@ __device__ __forceinline__ int4 cell_value(const CellTask &t, uint32_t u, int cx
 template <int C, int B>
 __device__ __forceinline__ void build_cells(const FrameArgs &a, int4 *cells, int l_hi, int l_lo,
                                             int base_hi, int xa, int xb, int ya, int yb,
-                                            int cxo, int cyo, int k0 = 0) {
+                                            int cxo, int cyo, int k0 = 0, int total = -1) {
     using F = GuideFmt<C, B>;
-    const int total = cell_count(l_hi, l_lo, xa, xb, ya, yb);
+    if (total < 0) total = cell_count(l_hi, l_lo, xa, xb, ya, yb);
 #pragma unroll 2
     for (int k = k0 + (int)threadIdx.x; k < total; k += kThreads) {
         const CellTask t = cell_task(a, k, l_hi, xa, xb, ya, yb);
@@ -225,37 +225,41 @@ struct Segs {
     static constexpr int NS = RW * NSY;
     __device__ __forceinline__ static int rx(int s) { return s % RW; }
     __device__ __forceinline__ static int ry(int s) { return 4 * (s / RW) - kPad + R; }
-    // bit j: row ry + j lies in the region
-    __device__ __forceinline__ static uint32_t rows(int ry) {
-        uint32_t m = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) m |= (uint32_t)(ry + j >= 0 && ry + j < RH) << j;
-        return m;
+    // bit j: lo <= ry + j < hi
+    __device__ __forceinline__ static uint32_t span(int ry, int lo, int hi) {
+        const int a = min(max(lo - ry, 0), 4), b = min(max(hi - ry, 0), 4);
+        return ((1u << b) - 1u) & ~((1u << a) - 1u);
     }
-    // bit j: pixel (rx, ry + j) lies in the region and in the W x H target
-    __device__ __forceinline__ static uint32_t mask(int rx, int ry, int rx0, int ry0, int W,
-                                                    int H) {
-        const bool col = rx0 + rx >= 0 && rx0 + rx < W;
-        uint32_t m = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int y = ry + j;
-            m |= (uint32_t)(col && y >= 0 && y < RH && ry0 + y >= 0 && ry0 + y < H) << j;
-        }
-        return m;
+    // bit j: row ry + j lies in the region
+    __device__ __forceinline__ static uint32_t rows(int ry) { return span(ry, 0, RH); }
+};
+
+// The region's columns [c_lo, c_hi) and rows [r_lo, r_hi) inside the target.
+struct TileBounds {
+    int c_lo, c_hi, r_lo, r_hi;
+    template <int R>
+    __device__ __forceinline__ static TileBounds of(int rx0, int ry0, int W, int H) {
+        return TileBounds{max(0, -rx0), min(kTW + 2 * R, W - rx0), max(0, -ry0),
+                          min(kTH + 2 * R, H - ry0)};
+    }
+    // bit j: pixel (rx, ry + j) of a segment lies in the region and the target
+    template <int R>
+    __device__ __forceinline__ uint32_t mask(int rx, int ry) const {
+        return rx >= c_lo && rx < c_hi ? Segs<R>::span(ry, r_lo, r_hi) : 0u;
     }
 };
 
-// Candidate test of the pixels of one segment: pixel j sits at region index
-// ibase + j * RW and its candidate source position is (sx[j], sy[j]).
-// Accepted pixels get A (and the level); the bits of rejected pixels of m
-// are returned.
 // The source side of a candidate test.
 struct SrcView {
     const uint32_t *src_packed;
     int Ws, Hs;
     uint64_t threshold;
 };
+
+// Candidate test of the pixels of one segment: pixel j sits at region index
+// ibase + j * RW and its candidate source position is (sx[j], sy[j]).
+// Accepted pixels get A (and the level); the bits of rejected pixels of m
+// are returned.
 
 template <int C, int B, int RW>
 __device__ __forceinline__ uint32_t test_segment(const SrcView &a, const uint32_t *gt,
@@ -422,8 +426,9 @@ template <int C, int B, int R, bool kTop>
 __device__ __forceinline__ void level_segments(const FrameArgs &a, const uint32_t *gt,
                                                uint32_t *A, uint8_t *lev, const int4 *cells,
                                                int base, const LevelCells &g, int l, int rx0,
-                                               int ry0, uint32_t t32, const uint16_t *list_in,
-                                               int n_in, uint16_t *list_out, int *cnt_out) {
+                                               int ry0, const TileBounds &tb, uint32_t t32,
+                                               const uint16_t *list_in, int n_in,
+                                               uint16_t *list_out, int *cnt_out) {
     using S = Segs<R>;
     const int n = kTop ? S::NS : n_in;
     for (int s0 = 0; s0 < n; s0 += kThreads) {
@@ -433,7 +438,7 @@ __device__ __forceinline__ void level_segments(const FrameArgs &a, const uint32_
         if (jj < n) {
             if constexpr (kTop) {
                 sg = jj;
-                m = S::mask(S::rx(sg), S::ry(sg), rx0, ry0, a.W, a.H);
+                m = tb.template mask<R>(S::rx(sg), S::ry(sg));
             } else {
                 const uint32_t e = list_in[jj];
                 sg = (int)(e >> 4);
@@ -470,6 +475,7 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     const uint32_t t32 = a.threshold > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)a.threshold;
     const int L_top = a.levels;
     const int eager_lo = L_top <= kEagerMinLevel ? 1 : kEagerMinLevel;
+    const TileBounds tb = TileBounds::of<R>(rx0, ry0, a.W, a.H);
 
     if (tid == 0) {
         cnt[0] = 0;
@@ -492,7 +498,7 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     for (int q = 0; q < kSegIters; ++q) {
         const int sg = q * kThreads + tid;
         const int rx = Segs<R>::rx(sg), ry = Segs<R>::ry(sg);
-        const uint32_t it = sg < Segs<R>::NS ? Segs<R>::mask(rx, ry, rx0, ry0, a.W, a.H) : 0u;
+        const uint32_t it = sg < Segs<R>::NS ? tb.template mask<R>(rx, ry) : 0u;
         itq[q] = it;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -515,7 +521,8 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
         }
     }
     if (has_cell) cells[tid] = cell_value(ct, cu, cxo, cyo);
-    build_cells<C, B>(a, cells, L_top, eager_lo, 0, xa, xb, ya, yb, cxo, cyo, kThreads);
+    if (n_eager > kThreads)
+        build_cells<C, B>(a, cells, L_top, eager_lo, 0, xa, xb, ya, yb, cxo, cyo, kThreads, n_eager);
     __syncthreads();
 
     // level step t (0 = top) appends to counter t % 3; the counter of step
@@ -525,7 +532,7 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     {
         // top level over every segment (cells of the top level start at 0)
         const LevelCells g = level_cells(L_top, xa, xb, ya, yb);
-        level_segments<C, B, R, true>(a, gt, A, lev, cells, 0, g, L_top, rx0, ry0, t32,
+        level_segments<C, B, R, true>(a, gt, A, lev, cells, 0, g, L_top, rx0, ry0, tb, t32,
                                       nullptr, 0, list1, &cnt[0]);
         __syncthreads();
         n_pend = cnt[0];
@@ -541,8 +548,8 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
             __syncthreads();
         }
         if (tid == 0) cnt[(t + 1) % 3] = 0;
-        level_segments<C, B, R, false>(a, gt, A, lev, cells, base, g, l, rx0, ry0, t32, list_cur,
-                                       n_pend, list_nxt, &cnt[t % 3]);
+        level_segments<C, B, R, false>(a, gt, A, lev, cells, base, g, l, rx0, ry0, tb, t32,
+                                       list_cur, n_pend, list_nxt, &cnt[t % 3]);
         __syncthreads();
         n_pend = cnt[t % 3];
         base += g.ncx * g.ncy;
