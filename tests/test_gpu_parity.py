@@ -233,8 +233,7 @@ def test_full_size_sampled_parity_and_properties(cuda_device, name):
 # lookup-only comparator (Section 4: texture mapping)
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("case", ["u8x3-48x40-L3-T12000-r1", "u16x2-40x36-L5-T4096-r3",
-                                  "u8x1-31x17-L2-T10-r0"])
+@pytest.mark.parametrize("case", REGRESSION_CASES)
 def test_lookup_only_matches_oracle(cuda_device, case):
     c = make_case(case)
     gt, gs, st = to_dev(c["tgt"], cuda_device), to_dev(c["src"], cuda_device), to_dev(c["style"], cuda_device)
@@ -243,6 +242,26 @@ def test_lookup_only_matches_oracle(cuda_device, case):
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(),
                           oracle.lookup_only(c["tgt"], c["src"], c["style"], c["key_bits"]))
+
+
+@pytest.mark.parametrize("W,H,channels,offset", [
+    (1028, 5, 3, 0),   # four pixels per thread with vector loads; two CTAs per row
+    (1030, 7, 3, 0),   # width not a multiple of 4: per-pixel loads
+    (515, 3, 2, 1),    # rows start one pixel in: unaligned
+    (260, 4, 4, 0), (261, 3, 1, 0)])
+def test_lookup_only_vector_and_ragged_rows(cuda_device, W, H, channels, offset):
+    """The comparator's vector path (aligned rows, width a multiple of 4) and
+    its per-pixel path give the same pixels as the oracle."""
+    big = synth.random_guide(W + channels, H, W + offset, channels)
+    tgt = np.ascontiguousarray(big)
+    src = synth.random_guide(W + 1, 20, 30, channels)
+    style = synth.random_style(W + 2, 20, 30)
+    gs, st = to_dev(src, cuda_device), to_dev(style, cuda_device)
+    lut = sb.build_lut(gs, 5)
+    gt = to_dev(tgt, cuda_device)[:, offset:]
+    out = sb.lookup_only(gt, gs, st, lut)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), oracle.lookup_only(tgt[:, offset:], src, style, 5))
 
 
 def test_lookup_only_full_size_sampled(cuda_device):
