@@ -38,6 +38,7 @@ import synth  # noqa: E402
 
 L2_BYTES = 126 * 1024 * 1024
 FRAMES_PER_STEP = 24
+E2E_GROUP = 4        # frames per batch launch on the end-to-end leg (24 frames: two groups per stream)
 METRIC = "Mpixel/s stylized (1080p/4K, blend on) and % HBM roofline; served p50/p99 latency"
 
 
@@ -426,19 +427,19 @@ def run_gpu(args):
                  "ms_per_step": ms_pf / pf_steps, "steps": pf_steps,
                  "launch": "CUDA graph of frames_per_step sb_stylize kernels (one per frame)"}
 
-    # end to end through the host-buffer call: pinned H2D, stylise, D2H, with
-    # frames spread over three streams so copies in both directions overlap
+    # end to end through the host-buffer batch call: groups of E2E_GROUP frames
+    # are copied in from pinned memory, stylised by one batch launch and copied
+    # out, consecutive groups on three streams so copies overlap kernels
     host_in = [torch.from_numpy(f.view(np.int16) if f.dtype == np.uint16 else f).pin_memory()
                for f in frames]
     host_out = [torch.empty((H, W, 4), dtype=torch.uint8).pin_memory() for _ in frames]
-    staging = [dict() for _ in frames]
+    staging = {}
     e2e_streams = [torch.cuda.Stream(dev) for _ in range(3)]
+    seeds = [w.seed + i for i in range(FRAMES_PER_STEP)]
 
     def e2e_step():
-        for i in range(FRAMES_PER_STEP):
-            sb.stylize_host(host_in[i], g_src, style, lut, w.levels, w.threshold,
-                            w.blend_radius, w.seed + i, host_out[i], staging=staging[i],
-                            stream=e2e_streams[i % 3])
+        sb.stylize_batch_host(host_in, lut, style, w.levels, w.threshold, seeds, w.blend_radius,
+                              host_out, group=E2E_GROUP, streams=e2e_streams, staging=staging)
 
     for _ in range(3):
         e2e_step()
@@ -510,7 +511,8 @@ def run_gpu(args):
                                        "(style + guide + table) once per launch"},
             "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
-                    "api": "stylize_host per frame (pinned host in/out), 3 streams"},
+                    "api": f"stylize_batch_host (pinned host in/out), groups of {E2E_GROUP} "
+                           "frames over 3 streams"},
             "issue_roofline": issue,
             "per_frame_launch": per_frame,
             "lookup_only": lookup,

@@ -26,7 +26,8 @@ import torch
 from . import _build
 
 __all__ = ["StyleBlitError", "Lut", "build_lut", "assign_chunks", "blend", "stylize",
-           "stylize_batch", "BatchFrame", "lookup_only", "stylize_host", "library_path", "load_library",
+           "stylize_batch", "BatchFrame", "lookup_only", "stylize_host", "stylize_batch_host",
+           "library_path", "load_library",
            "EXPORTED_SYMBOLS", "version", "MAX_BATCH"]
 
 MAX_BATCH = 128
@@ -318,6 +319,44 @@ def stylize_batch(frames, radius: int, stream=None):
                         f.seed & 0xFFFFFFFF, f.out.data_ptr())
     _check("sb_stylize_batch", lib.sb_stylize_batch(arr, len(frames), radius, _stream(stream)))
     return [f.out for f in frames]
+
+
+def stylize_batch_host(guides_host, luts, styles, levels, thresholds, seeds, radius: int,
+                       outs_host, group: int = 6, streams=None, staging: dict | None = None):
+    """Stylises frames held in pinned host memory into pinned host memory.
+
+    Frames go in groups of `group`: the group's guides are copied in, one
+    sb_stylize_batch launch stylises them, the RGBA8 results are copied out,
+    all enqueued on one of `streams` (consecutive groups on consecutive streams,
+    so one group's copies overlap the neighbouring groups' kernels).  `luts`,
+    `styles`, `levels`, `thresholds` and `seeds` are per frame (a single value
+    applies to every frame).  `staging` caches the device buffers between calls.
+    Returns `outs_host`; the caller synchronises the streams before reading it."""
+    n = len(guides_host)
+    per = lambda v: v if isinstance(v, (list, tuple)) else [v] * n
+    luts, styles, levels, thresholds, seeds = map(per, (luts, styles, levels, thresholds, seeds))
+    dev = styles[0].device
+    streams = list(streams) if streams else [torch.cuda.current_stream(dev)]
+    staging = {} if staging is None else staging
+    for g0 in range(0, n, group):
+        ks = range(g0, min(n, g0 + group))
+        stream = streams[(g0 // group) % len(streams)]
+        with torch.cuda.stream(stream):
+            frames = []
+            for k in ks:
+                key = (k, tuple(guides_host[k].shape), guides_host[k].dtype)
+                if key not in staging:
+                    staging[key] = (torch.empty(guides_host[k].shape, dtype=guides_host[k].dtype,
+                                                device=dev),
+                                    torch.empty(outs_host[k].shape, dtype=torch.uint8, device=dev))
+                g, o = staging[key]
+                g.copy_(guides_host[k], non_blocking=True)
+                frames.append(BatchFrame(g, luts[k], styles[k], levels[k], thresholds[k], seeds[k],
+                                         out=o))
+            stylize_batch(frames, radius, stream=stream)
+            for k, f in zip(ks, frames):
+                outs_host[k].copy_(f.out, non_blocking=True)
+    return outs_host
 
 
 def stylize_host(tgt_guide_host: torch.Tensor, src_guide, style, lut: Lut, levels: int,

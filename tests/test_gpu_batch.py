@@ -84,3 +84,38 @@ def test_batch_argument_errors(cuda_device):
     with pytest.raises(sb.StyleBlitError):
         sb.stylize_batch([f_ok] * (sb.MAX_BATCH + 1), 1)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("group,n_streams", [(2, 2), (3, 1), (7, 3)])
+def test_host_buffer_calls_equal_device_calls(cuda_device, group, n_streams):
+    """stylize_host and stylize_batch_host (pinned host in and out, copies and
+    launches on the given streams) give the device calls' pixels."""
+    exs = _exemplars(cuda_device, 2)
+    rng = np.random.default_rng(group)
+    guides, luts, styles, levels, Ts, seeds = [], [], [], [], [], []
+    for k in range(7):
+        W, H = int(rng.integers(30, 250)), int(rng.integers(20, 150))
+        guides.append(synth.bump_normals(500 + k, H, W, 3, (6.0, 40.0)))
+        e = exs[k % 2]
+        luts.append(e[4])
+        styles.append(e[3])
+        levels.append(int(rng.integers(1, 7)))
+        Ts.append(int(rng.integers(0, 2000)))
+        seeds.append(int(rng.integers(0, 2**32)))
+    host_in = [torch.from_numpy(g).pin_memory() for g in guides]
+    host_out = [torch.empty((g.shape[0], g.shape[1], 4), dtype=torch.uint8).pin_memory()
+                for g in guides]
+    streams = [torch.cuda.Stream(cuda_device) for _ in range(n_streams)]
+    sb.stylize_batch_host(host_in, luts, styles, levels, Ts, seeds, 2, host_out, group=group,
+                          streams=streams)
+    torch.cuda.synchronize()
+    single_out = [torch.empty_like(o).pin_memory() for o in host_out]
+    for k in range(7):
+        sb.stylize_host(host_in[k], exs[k % 2][2], styles[k], luts[k], levels[k], Ts[k], 2,
+                        seeds[k], single_out[k], stream=streams[k % n_streams])
+    torch.cuda.synchronize()
+    for k in range(7):
+        ref = sb.stylize(to_dev(guides[k], cuda_device), exs[k % 2][2], styles[k], luts[k],
+                         levels[k], Ts[k], 2, seeds[k]).cpu()
+        assert torch.equal(host_out[k], ref), f"frame {k}"
+        assert torch.equal(single_out[k], ref), f"frame {k}"
