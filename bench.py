@@ -52,6 +52,8 @@ def _args():
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-served", action="store_true")
+    p.add_argument("--no-uneven", action="store_true",
+                   help="skip the uneven batch (64 mixed-size frames, 8 exemplars)")
     p.add_argument("--profile-once", action="store_true",
                    help="build the step's frames and launch sb_stylize_batch twice, no timing "
                         "(a fixed launch sequence for ncu captures)")
@@ -521,6 +523,8 @@ def run_gpu(args):
             "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_served:
         line["served"] = run_served(dev)
+    if rank == 0 and world == 1 and not args.no_uneven:
+        line["batched_uneven"] = run_uneven(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = cpu_oracle_run(w, frames)
         line["cpu_baseline"] = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -529,6 +533,79 @@ def run_gpu(args):
     lut.destroy()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_uneven(dev, n_frames: int = 64, n_exemplars: int = 8, seed: int = 4000,
+               steps: int = 20) -> dict:
+    """The uneven batch: n_frames frames with widths uniform in [640, 3840]
+    (16:9), each stylised with one of n_exemplars 1024^2 sphere-guide
+    exemplars, L=6, T=300, 5x5 blend.  Frames are crops of two generated
+    3840x2160 normal fields.  Times per step: one sb_stylize per frame (a CUDA
+    graph of n_frames launches), one default batch launch, and the batch launch
+    under the schedule sb_autotune_batch picks (each a CUDA graph); checks that
+    the three give the same pixels."""
+    import torch
+
+    import paper_1807_03249_gb300 as sb
+    exs = []
+    for k in range(n_exemplars):
+        ex = synth.normal_exemplar(seed + 100 + k, 1024, strokes=100, octaves=3, lut_bits=6)
+        gs, st = torch.from_numpy(ex.guide).to(dev), torch.from_numpy(ex.style).to(dev)
+        exs.append((gs, st, sb.build_lut(gs, ex.lut_bits)))
+    fields = [synth.bump_normals(seed + k, 2160, 3840, 64, (20.0, 200.0)) for k in range(2)]
+    sizes = synth.batch_frame_sizes(seed, n_frames)
+    rng = np.random.default_rng(seed + 1)
+    frames, singles = [], []
+    for i, (w_, h_) in enumerate(sizes):
+        f = fields[i % 2]
+        y0, x0 = int(rng.integers(0, 2160 - h_ + 1)), int(rng.integers(0, 3840 - w_ + 1))
+        g = torch.from_numpy(np.ascontiguousarray(f[y0:y0 + h_, x0:x0 + w_])).to(dev)
+        gs, st, lut = exs[int(rng.integers(0, n_exemplars))]
+        sd = int(rng.integers(0, 2**32))
+        frames.append(sb.BatchFrame(g, lut, st, 6, 300, sd))
+        singles.append((g, gs, st, lut, sd, torch.empty_like(frames[-1].out)))
+    px = sum(f.tgt_guide.shape[0] * f.tgt_guide.shape[1] for f in frames)
+    stream = torch.cuda.Stream(dev)
+
+    def per_frame():
+        for g, gs, st, lut, sd, o in singles:
+            sb.stylize(g, gs, st, lut, 6, 300, 2, sd, out=o)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            fn()
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ms_pf = timed(per_frame)
+    ms_batch = timed(lambda: sb.stylize_batch(frames, 2))
+    best, _ = sb.autotune_batch(frames, 2, reps=3)
+    ms_tuned = timed(lambda: sb.stylize_batch(frames, 2, schedule=best))
+    torch.cuda.synchronize()
+    equal = all(torch.equal(f.out, o) for f, (_, _, _, _, _, o) in zip(frames, singles))
+    for _, _, lut in exs:
+        lut.destroy()
+    return {"frames": n_frames, "exemplars": n_exemplars, "mpixel_per_step": px / 1e6,
+            "per_frame_launch_frames_per_s": n_frames / (ms_pf / 1e3),
+            "batch_frames_per_s": n_frames / (ms_batch / 1e3),
+            "autotuned_frames_per_s": n_frames / (ms_tuned / 1e3),
+            "autotuned_mpixel_per_s": px / (ms_tuned / 1e3) / 1e6,
+            "autotuned_schedule": best, "equal_outputs": equal,
+            "ms_per_step": {"per_frame": ms_pf, "batch": ms_batch, "autotuned": ms_tuned},
+            "workload": f"{n_frames} frames 640x360..3840x2160 (16:9), {n_exemplars} 1024^2 "
+                        "sphere exemplars, L6 T300 5x5; each form a CUDA graph"}
 
 
 def run_served(dev, n_requests: int = 10000, rate_hz: float = 2000.0, pool: int = 64,

@@ -257,6 +257,49 @@ SB_API sb_status sb_stylize_batch(const sb_frame *frames, int32_t n_frames, int3
                                   sb_stream stream);
 
 /*
+ * Launch schedule of a batch.  The paper has no counterpart: this is a GPU
+ * scheduling choice, and every schedule gives the same pixels (each tile runs
+ * the same code).
+ *   persistent     0: one CTA per tile (the hardware issues tiles as CTAs
+ *                  retire); 1: as many CTAs as fit on the device take tiles
+ *                  from a work queue in device memory until the batch is done.
+ *                  At most 64 persistent launches may be in flight at once
+ *                  (each takes one of 64 queue slots in turn); the queue
+ *                  resets itself at the end of a launch, so CUDA graph replays
+ *                  are fine.
+ *   largest_first  0: tiles in frame order; 1: frames with more tiles first
+ *                  (shorter tail for uneven batches).
+ */
+typedef struct {
+    int32_t persistent;
+    int32_t largest_first;
+} sb_batch_schedule;
+
+/*
+ * sb_stylize_batch_sched -- sb_stylize_batch with an explicit schedule
+ * (NULL: {0, 0}, the schedule of sb_stylize_batch).  Same arguments, outputs
+ * and errors as sb_stylize_batch.
+ */
+SB_API sb_status sb_stylize_batch_sched(const sb_frame *frames, int32_t n_frames,
+                                        int32_t blend_radius, const sb_batch_schedule *schedule,
+                                        sb_stream stream);
+
+/*
+ * sb_autotune_batch -- picks the fastest schedule for this batch (no
+ * counterpart in the paper).  Runs each of the four schedules once untimed and
+ * `reps` times between two CUDA events on `stream`, waits for the stream, and
+ * writes the fastest to *best and its mean time per batch (ms) to *best_ms
+ * (nullable).  The batch's outputs are written (every run writes the same
+ * pixels).  Blocks the calling thread; refuses a stream under capture.
+ *   reps  1..1000.
+ * Errors: those of sb_stylize_batch; SB_ERR_INVALID_ARG (NULL best, reps out
+ * of range, a capturing stream); SB_ERR_CUDA.
+ */
+SB_API sb_status sb_autotune_batch(const sb_frame *frames, int32_t n_frames,
+                                   int32_t blend_radius, int32_t reps, sb_batch_schedule *best,
+                                   float *best_ms, sb_stream stream);
+
+/*
  * sb_lookup_only -- the per-pixel mapping StyleBlit is compared with in
  * Section 4 (texture mapping; The Lit Sphere): every target pixel copies the
  * style at the table entry of its own guide value, C_T[p] = C_S[LUT(G_T[p])],

@@ -26,7 +26,8 @@ import torch
 from . import _build
 
 __all__ = ["StyleBlitError", "Lut", "build_lut", "assign_chunks", "blend", "stylize",
-           "stylize_batch", "BatchFrame", "lookup_only", "stylize_host", "stylize_batch_host",
+           "stylize_batch", "autotune_batch", "BatchFrame", "lookup_only", "stylize_host",
+           "stylize_batch_host",
            "library_path", "load_library",
            "EXPORTED_SYMBOLS", "version", "MAX_BATCH"]
 
@@ -37,7 +38,8 @@ _STATUS = {0: "SB_OK", -1: "SB_ERR_INVALID_ARG", -2: "SB_ERR_UNSUPPORTED", -3: "
            -4: "SB_ERR_OOM", -5: "SB_ERR_TIMEOUT"}
 
 EXPORTED_SYMBOLS = ["sb_build_lut", "sb_build_lut_keyed", "sb_build_lut_noalloc", "sb_lut_destroy", "sb_lut_info",
-                    "sb_assign_chunks", "sb_blend", "sb_stylize", "sb_stylize_batch", "sb_lookup_only",
+                    "sb_assign_chunks", "sb_blend", "sb_stylize", "sb_stylize_batch",
+                    "sb_stylize_batch_sched", "sb_autotune_batch", "sb_lookup_only",
                     "sb_status_string", "sb_last_error", "sb_version"]
 
 
@@ -56,6 +58,10 @@ class _Guide(ctypes.Structure):
 class _Rgba8(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("width", ctypes.c_int32),
                 ("height", ctypes.c_int32), ("row_stride", ctypes.c_int64)]
+
+
+class _Schedule(ctypes.Structure):
+    _fields_ = [("persistent", ctypes.c_int32), ("largest_first", ctypes.c_int32)]
 
 
 class _Frame(ctypes.Structure):
@@ -100,6 +106,9 @@ def load_library(build_if_missing: bool = True):
             "sb_stylize": (ctypes.c_int, [P(_Guide), P(_Guide), P(_Rgba8), vp, i32, u64, i32,
                                           u32, vp, vp]),
             "sb_stylize_batch": (ctypes.c_int, [P(_Frame), i32, i32, vp]),
+            "sb_stylize_batch_sched": (ctypes.c_int, [P(_Frame), i32, i32, P(_Schedule), vp]),
+            "sb_autotune_batch": (ctypes.c_int, [P(_Frame), i32, i32, i32, P(_Schedule),
+                                                 P(ctypes.c_float), vp]),
             "sb_lookup_only": (ctypes.c_int, [P(_Guide), P(_Guide), P(_Rgba8), vp, vp, vp]),
             "sb_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "sb_last_error": (ctypes.c_char_p, []),
@@ -307,22 +316,49 @@ class BatchFrame:
         self.out = out
 
 
-def stylize_batch(frames, radius: int, stream=None):
-    """Stylises up to MAX_BATCH frames (BatchFrame) in one launch; returns their
-    outputs.  Frames share the guide format and the blend radius."""
-    lib = load_library()
-    frames = list(frames)
+def _frames_array(frames):
     arr = (_Frame * max(1, len(frames)))()
     for k, f in enumerate(frames):
         arr[k] = _Frame(_guide(f.tgt_guide, f"frames[{k}].tgt_guide"), f.lut.handle,
                         _style(f.style, f"frames[{k}].style"), f.levels, int(f.threshold),
                         f.seed & 0xFFFFFFFF, f.out.data_ptr())
-    _check("sb_stylize_batch", lib.sb_stylize_batch(arr, len(frames), radius, _stream(stream)))
+    return arr
+
+
+def stylize_batch(frames, radius: int, stream=None, schedule: dict | None = None):
+    """Stylises up to MAX_BATCH frames (BatchFrame) in one launch; returns their
+    outputs.  Frames share the guide format and the blend radius.  `schedule`
+    ({"persistent": 0/1, "largest_first": 0/1}, e.g. from autotune_batch)
+    picks the launch form; every schedule gives the same pixels."""
+    lib = load_library()
+    frames = list(frames)
+    arr = _frames_array(frames)
+    if schedule is None:
+        _check("sb_stylize_batch", lib.sb_stylize_batch(arr, len(frames), radius, _stream(stream)))
+    else:
+        sc = _Schedule(int(schedule.get("persistent", 0)), int(schedule.get("largest_first", 0)))
+        _check("sb_stylize_batch_sched",
+               lib.sb_stylize_batch_sched(arr, len(frames), radius, ctypes.byref(sc),
+                                          _stream(stream)))
     return [f.out for f in frames]
 
 
+def autotune_batch(frames, radius: int, reps: int = 5, stream=None):
+    """Times the launch schedules on this batch (writing its outputs) and
+    returns (fastest schedule as a dict, its mean ms per batch)."""
+    lib = load_library()
+    frames = list(frames)
+    arr = _frames_array(frames)
+    best, ms = _Schedule(), ctypes.c_float()
+    _check("sb_autotune_batch", lib.sb_autotune_batch(arr, len(frames), radius, reps,
+                                                      ctypes.byref(best), ctypes.byref(ms),
+                                                      _stream(stream)))
+    return {"persistent": best.persistent, "largest_first": best.largest_first}, ms.value
+
+
 def stylize_batch_host(guides_host, luts, styles, levels, thresholds, seeds, radius: int,
-                       outs_host, group: int = 6, streams=None, staging: dict | None = None):
+                       outs_host, group: int = 6, streams=None, staging: dict | None = None,
+                       schedule: dict | None = None):
     """Stylises frames held in pinned host memory into pinned host memory.
 
     Frames go in groups of `group`: the group's guides are copied in, one
@@ -330,8 +366,9 @@ def stylize_batch_host(guides_host, luts, styles, levels, thresholds, seeds, rad
     all enqueued on one of `streams` (consecutive groups on consecutive streams,
     so one group's copies overlap the neighbouring groups' kernels).  `luts`,
     `styles`, `levels`, `thresholds` and `seeds` are per frame (a single value
-    applies to every frame).  `staging` caches the device buffers between calls.
-    Returns `outs_host`; the caller synchronises the streams before reading it."""
+    applies to every frame).  `staging` caches the device buffers between calls;
+    `schedule` is passed to stylize_batch.  Returns `outs_host`; the caller
+    synchronises the streams before reading it."""
     n = len(guides_host)
     per = lambda v: v if isinstance(v, (list, tuple)) else [v] * n
     luts, styles, levels, thresholds, seeds = map(per, (luts, styles, levels, thresholds, seeds))
@@ -353,7 +390,7 @@ def stylize_batch_host(guides_host, luts, styles, levels, thresholds, seeds, rad
                 g.copy_(guides_host[k], non_blocking=True)
                 frames.append(BatchFrame(g, luts[k], styles[k], levels[k], thresholds[k], seeds[k],
                                          out=o))
-            stylize_batch(frames, radius, stream=stream)
+            stylize_batch(frames, radius, stream=stream, schedule=schedule)
             for k, f in zip(ks, frames):
                 outs_host[k].copy_(f.out, non_blocking=True)
     return outs_host

@@ -883,11 +883,10 @@ struct BatchArgs {
     FrameArgs f[kMaxBatch];
 };
 
+// Tile t of a batch: the frame k with tile_start[k] <= t < tile_start[k + 1].
 template <int C, int B, int R>
-__global__ void __launch_bounds__(kThreads, min_ctas(R))
-    batch_kernel(const __grid_constant__ BatchArgs b, const SmemLayout L) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int t = (int)blockIdx.x;
+__device__ __forceinline__ void batch_tile(const BatchArgs &b, const SmemLayout &L, int t,
+                                           unsigned char *smem) {
     int lo = 0, hi = b.n - 1;  // last frame whose first tile is <= t
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -897,6 +896,49 @@ __global__ void __launch_bounds__(kThreads, min_ctas(R))
     const FrameArgs a = b.f[lo];  // register copy: field reads become plain operands
     const int lt = t - b.tile_start[lo];
     frame_tile<C, B, kStylize, R>(a, L, lt % b.tiles_x[lo], lt / b.tiles_x[lo], smem);
+}
+
+template <int C, int B, int R>
+__global__ void __launch_bounds__(kThreads, min_ctas(R))
+    batch_kernel(const __grid_constant__ BatchArgs b, const SmemLayout L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    batch_tile<C, B, R>(b, L, (int)blockIdx.x, smem);
+}
+
+// Work queues of persistent batch launches: CTAs take the next tile from
+// `next` until the batch is exhausted; the last CTA to leave clears the queue
+// for the next launch (CUDA graph replays included).  A launch uses slot
+// `slot`; launches in flight at the same time need distinct slots.  No CTA
+// waits on another.
+struct TileQueue {
+    unsigned int next, done;
+};
+constexpr int kQueueSlots = 64;
+static __device__ TileQueue g_tile_queues[kQueueSlots];
+
+template <int C, int B, int R>
+__global__ void __launch_bounds__(kThreads, min_ctas(R))
+    batch_kernel_persistent(const __grid_constant__ BatchArgs b, const SmemLayout L, int slot) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int tile;
+    TileQueue &q = g_tile_queues[slot];
+    const int n_tiles = b.tile_start[b.n];
+    for (;;) {
+        if (threadIdx.x == 0) tile = (int)atomicAdd(&q.next, 1u);
+        __syncthreads();
+        const int t = tile;
+        __syncthreads();  // every thread has read `tile` before it is overwritten
+        if (t >= n_tiles) break;
+        batch_tile<C, B, R>(b, L, t, smem);
+        __syncthreads();  // the tile's shared memory is free before the next tile writes it
+    }
+    if (threadIdx.x == 0) {
+        // this CTA takes no more tiles; the last one out resets the queue
+        if (atomicAdd(&q.done, 1u) == gridDim.x - 1) {
+            atomicExch(&q.next, 0u);
+            atomicExch(&q.done, 0u);
+        }
+    }
 }
 
 template <bool F32, int R>
@@ -953,28 +995,61 @@ cudaError_t launch_stylize_r(const FrameArgs &a, cudaStream_t s) {
     return launch_tiles<frame_kernel<C, B, kStylize, R>>(L.total, a.W, a.H, s, a, L);
 }
 
+// CTAs of a persistent launch: as many as fit on the device at once (cached
+// per kernel, device and shared-memory size), at most one per tile.
+template <auto Kernel>
+int persistent_grid(size_t smem, int n_tiles) {
+    constexpr int kMaxDev = 64;
+    static std::atomic<uint64_t> cache[kMaxDev] = {};  // smem << 32 | CTAs
+    int dev = 0;
+    cudaGetDevice(&dev);
+    uint64_t c = dev < kMaxDev ? cache[dev].load(std::memory_order_relaxed) : 0;
+    int ctas = 0;
+    if (c && (c >> 32) == smem) {
+        ctas = (int)(c & 0xFFFFFFFFu);
+    } else {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, Kernel, kThreads, smem);
+        ctas = max(1, sms * max(per_sm, 1));
+        if (dev < kMaxDev) cache[dev].store(((uint64_t)smem << 32) | (uint32_t)ctas);
+    }
+    return min(ctas, n_tiles);
+}
+
 template <int C, int B, int R>
-cudaError_t launch_batch_r(const BatchArgs &b, int max_levels, cudaStream_t s) {
+cudaError_t launch_batch_r(const BatchArgs &b, int max_levels, bool persistent, cudaStream_t s) {
     // one layout (for the deepest frame) serves every tile of the launch
     const SmemLayout L = smem_layout(R, max_levels);
-    cudaError_t e = ensure_smem<batch_kernel<C, B, R>>(L.total);
+    const int n_tiles = b.tile_start[b.n];
+    if (!persistent) {
+        cudaError_t e = ensure_smem<batch_kernel<C, B, R>>(L.total);
+        if (e != cudaSuccess) return e;
+        batch_kernel<C, B, R><<<n_tiles, kThreads, L.total, s>>>(b, L);
+        return cudaGetLastError();
+    }
+    cudaError_t e = ensure_smem<batch_kernel_persistent<C, B, R>>(L.total);
     if (e != cudaSuccess) return e;
-    batch_kernel<C, B, R><<<b.tile_start[b.n], kThreads, L.total, s>>>(b, L);
+    static std::atomic<unsigned> next_slot{0};
+    const int slot = (int)(next_slot.fetch_add(1u) % kQueueSlots);
+    const int grid = persistent_grid<batch_kernel_persistent<C, B, R>>(L.total, n_tiles);
+    batch_kernel_persistent<C, B, R><<<grid, kThreads, L.total, s>>>(b, L, slot);
     return cudaGetLastError();
 }
 
 // Launches the batch kernel of guide format <C, B> for blend radius r.
 template <int C, int B>
-cudaError_t launch_batch(const BatchArgs &b, int r, int max_levels, cudaStream_t s) {
+cudaError_t launch_batch(const BatchArgs &b, int r, int max_levels, bool persistent,
+                         cudaStream_t s) {
     switch (r) {
-        case 0: return launch_batch_r<C, B, 0>(b, max_levels, s);
-        case 1: return launch_batch_r<C, B, 1>(b, max_levels, s);
-        case 2: return launch_batch_r<C, B, 2>(b, max_levels, s);
-        case 3: return launch_batch_r<C, B, 3>(b, max_levels, s);
-        case 4: return launch_batch_r<C, B, 4>(b, max_levels, s);
-        case 5: return launch_batch_r<C, B, 5>(b, max_levels, s);
-        case 6: return launch_batch_r<C, B, 6>(b, max_levels, s);
-        case 7: return launch_batch_r<C, B, 7>(b, max_levels, s);
+        case 0: return launch_batch_r<C, B, 0>(b, max_levels, persistent, s);
+        case 1: return launch_batch_r<C, B, 1>(b, max_levels, persistent, s);
+        case 2: return launch_batch_r<C, B, 2>(b, max_levels, persistent, s);
+        case 3: return launch_batch_r<C, B, 3>(b, max_levels, persistent, s);
+        case 4: return launch_batch_r<C, B, 4>(b, max_levels, persistent, s);
+        case 5: return launch_batch_r<C, B, 5>(b, max_levels, persistent, s);
+        case 6: return launch_batch_r<C, B, 6>(b, max_levels, persistent, s);
+        case 7: return launch_batch_r<C, B, 7>(b, max_levels, persistent, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -1001,12 +1076,18 @@ cudaError_t launch_frame(int mode, const FrameArgs &a, cudaStream_t s) {
 
 // per-format launchers, one translation unit each (sb_frame_c<C>b<B>.cu)
 // per-format batch launchers, defined next to the frame launchers
-cudaError_t launch_batch_c1b8(const BatchArgs &b, int r, int max_levels, cudaStream_t s);
-cudaError_t launch_batch_c2b8(const BatchArgs &b, int r, int max_levels, cudaStream_t s);
-cudaError_t launch_batch_c3b8(const BatchArgs &b, int r, int max_levels, cudaStream_t s);
-cudaError_t launch_batch_c4b8(const BatchArgs &b, int r, int max_levels, cudaStream_t s);
-cudaError_t launch_batch_c1b16(const BatchArgs &b, int r, int max_levels, cudaStream_t s);
-cudaError_t launch_batch_c2b16(const BatchArgs &b, int r, int max_levels, cudaStream_t s);
+cudaError_t launch_batch_c1b8(const BatchArgs &b, int r, int max_levels, bool persistent,
+                              cudaStream_t s);
+cudaError_t launch_batch_c2b8(const BatchArgs &b, int r, int max_levels, bool persistent,
+                              cudaStream_t s);
+cudaError_t launch_batch_c3b8(const BatchArgs &b, int r, int max_levels, bool persistent,
+                              cudaStream_t s);
+cudaError_t launch_batch_c4b8(const BatchArgs &b, int r, int max_levels, bool persistent,
+                              cudaStream_t s);
+cudaError_t launch_batch_c1b16(const BatchArgs &b, int r, int max_levels, bool persistent,
+                              cudaStream_t s);
+cudaError_t launch_batch_c2b16(const BatchArgs &b, int r, int max_levels, bool persistent,
+                              cudaStream_t s);
 cudaError_t launch_frame_c1b8(int mode, const FrameArgs &a, cudaStream_t s);
 cudaError_t launch_frame_c2b8(int mode, const FrameArgs &a, cudaStream_t s);
 cudaError_t launch_frame_c3b8(int mode, const FrameArgs &a, cudaStream_t s);

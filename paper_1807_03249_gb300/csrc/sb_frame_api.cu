@@ -1,6 +1,7 @@
 // C ABI entry points of the per-frame StyleBlit path (Algorithm 2 and the
 // voting step of Section 3.2): argument validation and kernel dispatch.  The
 // frame kernels live in sb_frame.cuh; the blend kernels are instantiated here.
+#include <algorithm>
 #include <climits>
 #include <cstdio>
 #include <string>
@@ -28,18 +29,18 @@ static cudaError_t launch_frame_any(int channels, int bits, int mode, const Fram
 }
 
 static cudaError_t launch_batch_any(int channels, int bits, const BatchArgs &b, int r,
-                                    int max_levels, cudaStream_t s) {
+                                    bool persistent, int max_levels, cudaStream_t s) {
     if (bits == 8) {
         switch (channels) {
-            case 1: return launch_batch_c1b8(b, r, max_levels, s);
-            case 2: return launch_batch_c2b8(b, r, max_levels, s);
-            case 3: return launch_batch_c3b8(b, r, max_levels, s);
-            case 4: return launch_batch_c4b8(b, r, max_levels, s);
+            case 1: return launch_batch_c1b8(b, r, max_levels, persistent, s);
+            case 2: return launch_batch_c2b8(b, r, max_levels, persistent, s);
+            case 3: return launch_batch_c3b8(b, r, max_levels, persistent, s);
+            case 4: return launch_batch_c4b8(b, r, max_levels, persistent, s);
         }
     } else if (bits == 16) {
         switch (channels) {
-            case 1: return launch_batch_c1b16(b, r, max_levels, s);
-            case 2: return launch_batch_c2b16(b, r, max_levels, s);
+            case 1: return launch_batch_c1b16(b, r, max_levels, persistent, s);
+            case 2: return launch_batch_c2b16(b, r, max_levels, persistent, s);
         }
     }
     return cudaErrorInvalidValue;
@@ -198,19 +199,25 @@ extern "C" sb_status sb_blend(const uint32_t *assign, int32_t tgt_w, int32_t tgt
     return ok();
 }
 
-extern "C" sb_status sb_stylize_batch(const sb_frame *frames, int32_t n_frames,
-                                      int32_t blend_radius, sb_stream stream) {
+// Validates a batch and fills the launch descriptor; frames go in the given
+// order or, with largest_first, by decreasing tile count (each frame keeps its
+// own output, so the order changes only which tiles are issued first).
+static sb_status prepare_batch(const sb_frame *frames, int32_t n_frames, int32_t blend_radius,
+                               bool largest_first, BatchArgs &b, int &max_levels,
+                               int &channels, int &bits) {
     if (n_frames < 0 || n_frames > kMaxBatch)
         return fail(SB_ERR_INVALID_ARG, "n_frames must be in [0, 128]");
     if (n_frames == 0) return ok();
     if (!frames) return fail(SB_ERR_INVALID_ARG, "frames: NULL");
     if (blend_radius < 0 || blend_radius > kMaxFusedRadius)
         return fail(SB_ERR_INVALID_ARG, "blend_radius must be in [0, 7]");
-    static thread_local BatchArgs b;  // ~18 KB: kept off the stack
     b.n = n_frames;
     b.tile_start[0] = 0;
-    int max_levels = 1;
-    const int channels = frames[0].tgt_guide.channels, bits = frames[0].tgt_guide.bits;
+    max_levels = 1;
+    channels = frames[0].tgt_guide.channels;
+    bits = frames[0].tgt_guide.bits;
+    int order[kMaxBatch];
+    int64_t tiles[kMaxBatch];
     char name[64];
     for (int k = 0; k < n_frames; ++k) {
         const sb_frame &f = frames[k];
@@ -232,28 +239,102 @@ extern "C" sb_status sb_stylize_batch(const sb_frame *frames, int32_t n_frames,
         const int64_t npx = (int64_t)f.tgt_guide.width * f.tgt_guide.height;
         if (npx > 0 && (!f.rgba8_out || ((uintptr_t)f.rgba8_out % 4)))
             return fail(SB_ERR_INVALID_ARG, std::string(name) + ": rgba8_out NULL or misaligned");
-        const int tx = (f.tgt_guide.width + kTW - 1) / kTW, ty = (f.tgt_guide.height + kTH - 1) / kTH;
-        const int64_t next = (int64_t)b.tile_start[k] + (npx > 0 ? (int64_t)tx * ty : 0);
+        const int64_t tx = (f.tgt_guide.width + kTW - 1) / kTW, ty = (f.tgt_guide.height + kTH - 1) / kTH;
+        tiles[k] = npx > 0 ? tx * ty : 0;
+        order[k] = k;
+        max_levels = max(max_levels, (int)f.levels);
+    }
+    if (largest_first)
+        std::stable_sort(order, order + n_frames, [&](int i, int j) { return tiles[i] > tiles[j]; });
+    for (int i = 0; i < n_frames; ++i) {
+        const sb_frame &f = frames[order[i]];
+        const int64_t next = (int64_t)b.tile_start[i] + tiles[order[i]];
         if (next > INT_MAX) return fail(SB_ERR_INVALID_ARG, "sb_stylize_batch: too many tiles");
-        b.tile_start[k + 1] = (int)next;
-        b.tiles_x[k] = tx > 0 ? tx : 1;
+        b.tile_start[i + 1] = (int)next;
+        b.tiles_x[i] = max(1, (f.tgt_guide.width + kTW - 1) / kTW);
         FrameArgs a = frame_args(&f.tgt_guide, f.lut, f.levels, f.threshold, f.seed);
         a.style = f.src_style.data;
         a.style_stride_px = (int)(f.src_style.row_stride / 4);
         a.radius = blend_radius;
         a.rgba_out = reinterpret_cast<uint32_t *>(f.rgba8_out);
-        b.f[k] = a;
-        max_levels = max(max_levels, (int)f.levels);
+        b.f[i] = a;
     }
-    if (b.tile_start[n_frames] == 0) return ok();
     int dev = 0;
     cudaGetDevice(&dev);
     for (int k = 0; k < n_frames; ++k)
         if (frames[k].lut->device != dev) return fail(SB_ERR_INVALID_ARG, "a lut lives on another device");
+    return ok();
+}
+
+extern "C" sb_status sb_stylize_batch_sched(const sb_frame *frames, int32_t n_frames,
+                                            int32_t blend_radius,
+                                            const sb_batch_schedule *schedule,
+                                            sb_stream stream) {
+    const sb_batch_schedule sched = schedule ? *schedule : sb_batch_schedule{0, 0};
+    static thread_local BatchArgs b;  // ~18 KB: kept off the stack
+    int max_levels = 1, channels = 0, bits = 0;
+    sb_status st = prepare_batch(frames, n_frames, blend_radius, sched.largest_first != 0, b,
+                                 max_levels, channels, bits);
+    if (st != SB_OK || n_frames == 0 || b.tile_start[n_frames] == 0) return st;
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) return cuda_fail(e, "pending CUDA error");
-    e = launch_batch_any(channels, bits, b, blend_radius, max_levels,
+    e = launch_batch_any(channels, bits, b, blend_radius, sched.persistent != 0, max_levels,
                          static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "sb_stylize_batch");
+    return ok();
+}
+
+extern "C" sb_status sb_stylize_batch(const sb_frame *frames, int32_t n_frames,
+                                      int32_t blend_radius, sb_stream stream) {
+    return sb_stylize_batch_sched(frames, n_frames, blend_radius, nullptr, stream);
+}
+
+extern "C" sb_status sb_autotune_batch(const sb_frame *frames, int32_t n_frames,
+                                       int32_t blend_radius, int32_t reps,
+                                       sb_batch_schedule *best, float *best_ms,
+                                       sb_stream stream) {
+    if (!best) return fail(SB_ERR_INVALID_ARG, "best: NULL");
+    if (reps < 1 || reps > 1000) return fail(SB_ERR_INVALID_ARG, "reps must be in [1, 1000]");
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "sb_autotune_batch");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(SB_ERR_INVALID_ARG, "sb_autotune_batch: the stream is being captured");
+    const sb_batch_schedule cand[4] = {{0, 0}, {0, 1}, {1, 0}, {1, 1}};
+    cudaEvent_t ev[2];
+    if ((e = cudaEventCreate(&ev[0])) != cudaSuccess) return cuda_fail(e, "sb_autotune_batch");
+    if ((e = cudaEventCreate(&ev[1])) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return cuda_fail(e, "sb_autotune_batch");
+    }
+    sb_status st = SB_OK;
+    float best_t = 0.f;
+    int best_i = 0;
+    for (int i = 0; i < 4 && st == SB_OK; ++i) {
+        // one untimed run, then reps timed runs between two events
+        st = sb_stylize_batch_sched(frames, n_frames, blend_radius, &cand[i], stream);
+        if (st == SB_OK) e = cudaEventRecord(ev[0], s);
+        for (int k = 0; k < reps && st == SB_OK; ++k)
+            st = sb_stylize_batch_sched(frames, n_frames, blend_radius, &cand[i], stream);
+        if (st != SB_OK) break;
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "sb_autotune_batch");
+            break;
+        }
+        if (i == 0 || t < best_t) {
+            best_t = t;
+            best_i = i;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (st != SB_OK) return st;
+    *best = cand[best_i];
+    if (best_ms) *best_ms = best_t / reps;
     return ok();
 }

@@ -5,7 +5,8 @@ namespace sb {
 cudaError_t launch_frame_c1b16(int mode, const FrameArgs &a, cudaStream_t s) {
     return launch_frame<1, 16>(mode, a, s);
 }
-cudaError_t launch_batch_c1b16(const BatchArgs &b, int r, int max_levels, cudaStream_t s) {
-    return launch_batch<1, 16>(b, r, max_levels, s);
+cudaError_t launch_batch_c1b16(const BatchArgs &b, int r, int max_levels, bool persistent,
+                              cudaStream_t s) {
+    return launch_batch<1, 16>(b, r, max_levels, persistent, s);
 }
 }  // namespace sb

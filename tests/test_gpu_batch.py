@@ -119,3 +119,71 @@ def test_host_buffer_calls_equal_device_calls(cuda_device, group, n_streams):
                          levels[k], Ts[k], 2, seeds[k]).cpu()
         assert torch.equal(host_out[k], ref), f"frame {k}"
         assert torch.equal(single_out[k], ref), f"frame {k}"
+
+
+def _uneven_batch(dev, n, seed):
+    """Frames of mixed sizes (some empty-ish and tiny), exemplars, levels
+    (1 and above 8 included), thresholds and seeds."""
+    rng = np.random.default_rng(seed)
+    exs = _exemplars(dev, 3)
+    frames = []
+    for k in range(n):
+        W, H = int(rng.integers(1, 700)), int(rng.integers(1, 400))
+        g = synth.bump_normals(1300 + k, H, W, 3, (6.0, 40.0))
+        e = exs[k % 3]
+        levels = [1, 9, 12][k % 3] if k < 3 else int(rng.integers(2, 8))
+        frames.append(sb.BatchFrame(to_dev(g, dev), e[4], e[3], levels,
+                                    int(rng.integers(0, 3000)), int(rng.integers(0, 2**32))))
+    return frames
+
+
+@pytest.mark.parametrize("radius", [1, 2, 3])
+def test_every_schedule_gives_the_same_pixels(cuda_device, radius):
+    """One CTA per tile or a persistent work queue, frame order or largest
+    frames first: bit-identical outputs."""
+    frames = _uneven_batch(cuda_device, 11, radius)
+    ref = [o.clone() for o in sb.stylize_batch(frames, radius)]
+    for persistent in (0, 1):
+        for largest_first in (0, 1):
+            for f in frames:
+                f.out.zero_()
+            outs = sb.stylize_batch(frames, radius,
+                                    schedule={"persistent": persistent,
+                                              "largest_first": largest_first})
+            torch.cuda.synchronize()
+            for k, (o, r) in enumerate(zip(outs, ref)):
+                assert torch.equal(o, r), f"schedule {persistent}{largest_first} frame {k}"
+
+
+def test_persistent_queue_resets_across_launches_and_graph_replays(cuda_device):
+    """The work queue clears itself at the end of each launch: more launches
+    than queue slots, and a captured graph replayed several times, still
+    cover every tile."""
+    frames = _uneven_batch(cuda_device, 6, 7)
+    ref = [o.clone() for o in sb.stylize_batch(frames, 2)]
+    sched = {"persistent": 1, "largest_first": 1}
+    for _ in range(70):  # more than the 64 queue slots
+        sb.stylize_batch(frames, 2, schedule=sched)
+    torch.cuda.synchronize()
+    assert all(torch.equal(o, r) for o, r in zip([f.out for f in frames], ref))
+    stream = torch.cuda.Stream(cuda_device)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        sb.stylize_batch(frames, 2, schedule=sched)
+    for _ in range(3):
+        for f in frames:
+            f.out.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert all(torch.equal(f.out, r) for f, r in zip(frames, ref))
+
+
+def test_autotune_picks_a_schedule_and_keeps_the_pixels(cuda_device):
+    frames = _uneven_batch(cuda_device, 8, 3)
+    ref = [o.clone() for o in sb.stylize_batch(frames, 2)]
+    best, ms = sb.autotune_batch(frames, 2, reps=2)
+    torch.cuda.synchronize()
+    assert best["persistent"] in (0, 1) and best["largest_first"] in (0, 1) and ms > 0
+    assert all(torch.equal(f.out, r) for f, r in zip(frames, ref))
+    with pytest.raises(sb.StyleBlitError):
+        sb.autotune_batch(frames, 2, reps=0)
