@@ -260,7 +260,6 @@ struct SrcView {
 // ibase + j * RW and its candidate source position is (sx[j], sy[j]).
 // Accepted pixels get A (and the level); the bits of rejected pixels of m
 // are returned.
-
 template <int C, int B, int RW>
 __device__ __forceinline__ uint32_t test_segment(const SrcView &a, const uint32_t *gt,
                                                  uint32_t *A, uint8_t *lev, int l, uint32_t t32,
@@ -357,8 +356,8 @@ __device__ __forceinline__ uint32_t segment_level_rare(const SrcView &a, const u
 // region (rx, ry): returns the rejected ones.  The packed keys of the nine
 // candidates are affine in p, so the pixels that pick a given seed form a
 // convex set: when the first and last pixel of m pick the same seed, every
-// pixel between them does and the nine-way search runs once.  Otherwise (and
-// at level 1, where the segment spans two cells) each pixel searches.
+// pixel between them does and the nine-way search runs once.  Otherwise each
+// pixel searches (level 1 and the unscaled levels: segment_level_rare).
 template <int C, int B, int R>
 __device__ __forceinline__ uint32_t segment_level(const FrameArgs &a, const uint32_t *gt,
                                                   uint32_t *A, uint8_t *lev, const int4 *cells,
