@@ -417,25 +417,25 @@ __device__ __forceinline__ uint32_t segment_level(const FrameArgs &a, const uint
     return test_segment<C, B, RW>(sv, gt, A, lev, l, t32, m, ibase, sx, sy);
 }
 
-// One level over segments: the top level visits every segment of the region
+// One level over segments: the top level (top) visits every segment of the region
 // (its in-target pixels), lower levels the list of segments with pending
 // pixels (entries: segment index << 4 | pixel mask).  Segments with rejected
 // pixels are appended to list_out.
-template <int C, int B, int R, bool kTop>
+template <int C, int B, int R>
 __device__ __forceinline__ void level_segments(const FrameArgs &a, const uint32_t *gt,
                                                uint32_t *A, uint8_t *lev, const int4 *cells,
                                                int base, const LevelCells &g, int l, int rx0,
                                                int ry0, const TileBounds &tb, uint32_t t32,
-                                               const uint16_t *list_in, int n_in,
+                                               bool top, const uint16_t *list_in, int n_in,
                                                uint16_t *list_out, int *cnt_out) {
     using S = Segs<R>;
-    const int n = kTop ? S::NS : n_in;
+    const int n = top ? S::NS : n_in;
     for (int s0 = 0; s0 < n; s0 += kThreads) {
         const int jj = s0 + (int)threadIdx.x;
         int sg = 0;
         uint32_t m = 0;
         if (jj < n) {
-            if constexpr (kTop) {
+            if (top) {
                 sg = jj;
                 m = tb.template mask<R>(S::rx(sg), S::ry(sg));
             } else {
@@ -526,20 +526,12 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
 
     // level step t (0 = top) appends to counter t % 3; the counter of step
     // t + 1 is cleared during step t (its last reader passed step t - 1's
-    // barrier), so one barrier per level publishes both the list and the reset
-    int n_pend, base;
-    {
-        // top level over every segment (cells of the top level start at 0)
-        const LevelCells g = level_cells(L_top, xa, xb, ya, yb);
-        level_segments<C, B, R, true>(a, gt, A, lev, cells, 0, g, L_top, rx0, ry0, tb, t32,
-                                      nullptr, 0, list1, &cnt[0]);
-        __syncthreads();
-        n_pend = cnt[0];
-        base = g.ncx * g.ncy;
-    }
-    const uint16_t *list_cur = list1;
-    uint16_t *list_nxt = list0;
-    for (int l = L_top - 1, t = 1; l >= 1 && n_pend > 0; --l, ++t) {
+    // barrier), so one barrier per level publishes both the list and the reset.
+    // The top level visits every segment of the region; its cells start at 0.
+    int n_pend = Segs<R>::NS, base = 0;
+    const uint16_t *list_cur = list0;
+    uint16_t *list_nxt = list1;
+    for (int l = L_top, t = 0; l >= 1 && n_pend > 0; --l, ++t) {
         const LevelCells g = level_cells(l, xa, xb, ya, yb);
         if (l == kEagerMinLevel - 1 && eager_lo > 1) {
             // a pixel still needs the fine levels: build levels 2 and 1 now
@@ -547,14 +539,14 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
             __syncthreads();
         }
         if (tid == 0) cnt[(t + 1) % 3] = 0;
-        level_segments<C, B, R, false>(a, gt, A, lev, cells, base, g, l, rx0, ry0, tb, t32,
-                                       list_cur, n_pend, list_nxt, &cnt[t % 3]);
+        level_segments<C, B, R>(a, gt, A, lev, cells, base, g, l, rx0, ry0, tb, t32, t == 0,
+                                list_cur, n_pend, list_nxt, &cnt[t % 3]);
         __syncthreads();
         n_pend = cnt[t % 3];
         base += g.ncx * g.ncy;
-        const uint16_t *tmp = list_cur;
+        const uint16_t *done = list_cur;
         list_cur = list_nxt;
-        list_nxt = const_cast<uint16_t *>(tmp);
+        list_nxt = const_cast<uint16_t *>(done);
     }
 }
 
