@@ -204,7 +204,7 @@ __device__ __forceinline__ void build_cells(const FrameArgs &a, int4 *cells, int
                                             int cxo, int cyo, int k0 = 0, int total = -1) {
     using F = GuideFmt<C, B>;
     if (total < 0) total = cell_count(l_hi, l_lo, xa, xb, ya, yb);
-#pragma unroll 2
+#pragma unroll 1
     for (int k = k0 + (int)threadIdx.x; k < total; k += kThreads) {
         const CellTask t = cell_task(a, k, l_hi, xa, xb, ya, yb);
         const uint32_t u = __ldg(
