@@ -525,6 +525,8 @@ def run_gpu(args):
         line["served"] = run_served(dev)
     if rank == 0 and world == 1 and not args.no_uneven:
         line["batched_uneven"] = run_uneven(dev)
+    if rank == 0:
+        line["workload_stats"] = workload_stats(sb, g_tgt[0], g_src, lut, w, w.blend_radius)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = cpu_oracle_run(w, frames)
         line["cpu_baseline"] = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -533,6 +535,41 @@ def run_gpu(args):
     lut.destroy()
     if world > 1:
         dist.destroy_process_group()
+
+
+def workload_stats(sb, g_tgt, g_src, lut, w, radius: int, n_sample: int = 20000,
+                   seed: int = 7) -> dict:
+    """Method statistics of one frame (from sb_assign_chunks): accepted-level
+    histogram and mean, and over a pixel sample the mean number of distinct
+    chunk translations A(n) - n in the vote window (1 = a plain copy) and the
+    share of windows with more than one."""
+    import torch
+    A, lev = sb.assign_chunks(g_tgt, g_src, lut, w.levels, w.threshold, w.seed)
+    torch.cuda.synchronize()
+    a = A.cpu().numpy().astype(np.int64)
+    lv = lev.cpu().numpy()
+    H, W = a.shape
+    hist = np.bincount(lv.ravel(), minlength=w.levels + 1)[1:]
+    ys, xs = np.mgrid[0:H, 0:W]
+    dx = (a & 0xFFFF) - xs
+    dy = (a >> 16) - ys
+    d = (dy + 65536) * 262144 + (dx + 65536)  # translation as one integer
+    rng = np.random.default_rng(seed)
+    px = rng.integers(0, W, n_sample)
+    py = rng.integers(0, H, n_sample)
+    counts = np.empty(n_sample, np.int64)
+    offs = np.arange(-radius, radius + 1)
+    for k in range(n_sample):
+        yy = np.clip(py[k] + offs, 0, H - 1)
+        xx = np.clip(px[k] + offs, 0, W - 1)
+        win = d[np.ix_(np.unique(yy), np.unique(xx))]
+        counts[k] = len(np.unique(win))
+    return {"level_histogram": {f"L{l + 1}": int(c) for l, c in enumerate(hist)},
+            "mean_accepted_level": float((np.arange(1, w.levels + 1) * hist).sum() / hist.sum()),
+            "mean_distinct_translations_per_window": float(counts.mean()),
+            "windows_with_several_translations": float((counts > 1).mean()),
+            "sample": f"frame 0, {n_sample} pixels for the window statistics (window clipped "
+                      "at frame borders)"}
 
 
 def run_uneven(dev, n_frames: int = 64, n_exemplars: int = 8, seed: int = 4000,
