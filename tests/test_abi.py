@@ -84,3 +84,27 @@ def test_invalid_blend_and_lut_arguments_are_rejected_on_the_host():
     assert lib.sb_build_lut(None, 6, ctypes.byref(h), None) == -1
     assert h.value is None
     assert lib.sb_lut_destroy(None) == 0
+
+
+def test_invalid_batch_and_schedule_arguments_are_rejected_on_the_host():
+    lib = sb.load_library()
+    frames = (sb._Frame * 1)()
+    sched = sb._Schedule(1, 1)
+    best, ms = sb._Schedule(), ctypes.c_float()
+    assert lib.sb_stylize_batch(frames, 129, 2, None) == -1            # too many frames
+    assert lib.sb_stylize_batch(None, 1, 2, None) == -1                # NULL frames
+    assert lib.sb_stylize_batch_sched(frames, 1, 8, ctypes.byref(sched), None) == -1  # radius
+    assert lib.sb_stylize_batch_sched(frames, -1, 2, None, None) == -1
+    assert lib.sb_stylize_batch_sched(frames, 0, 2, None, None) == 0   # empty batch: no-op
+    assert lib.sb_autotune_batch(frames, 1, 2, 3, None, ctypes.byref(ms), None) == -1  # no best
+    assert lib.sb_autotune_batch(frames, 1, 2, 0, ctypes.byref(best), None, None) == -1  # reps
+    assert b"reps" in lib.sb_last_error()
+
+
+def test_style_too_large_for_32_bit_offsets_is_rejected():
+    """The kernels address the style with 32-bit pixel offsets: height times
+    row stride must stay below 2^31 pixels."""
+    lib = sb.load_library()
+    st = sb._Rgba8(0x2000, 64, 64, 4 * (1 << 26))  # 64 rows of 2^26 pixels
+    assert lib.sb_blend(0x1000, 8, 8, ctypes.byref(st), 1, 0x3000, None, None) == -1
+    assert b"2^33" in lib.sb_last_error()
