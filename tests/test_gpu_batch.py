@@ -187,3 +187,32 @@ def test_autotune_picks_a_schedule_and_keeps_the_pixels(cuda_device):
     assert all(torch.equal(f.out, r) for f, r in zip(frames, ref))
     with pytest.raises(sb.StyleBlitError):
         sb.autotune_batch(frames, 2, reps=0)
+
+
+def test_every_schedule_gives_the_same_pixels_uv16(cuda_device):
+    """The same for 16-bit two-channel UV guides (the 4K format), 7x7 blend."""
+    src = synth.identity_uv_guide(96, 128)
+    style = synth.random_style(31, 96, 128)
+    gs, st = to_dev(src, cuda_device), to_dev(style, cuda_device)
+    lut = sb.build_lut(gs, 8)
+    rng = np.random.default_rng(5)
+    frames = []
+    for k in range(7):
+        W, H = int(rng.integers(40, 400)), int(rng.integers(30, 260))
+        g = synth.warped_uv_guide(600 + k, H, W, 96, 128, 8)
+        frames.append(sb.BatchFrame(to_dev(g, cuda_device), lut, st, int(rng.integers(2, 8)),
+                                    int(rng.integers(0, 1 << 21)), int(rng.integers(0, 2**32))))
+    ref = [o.clone() for o in sb.stylize_batch(frames, 3)]
+    for persistent in (0, 1):
+        for largest_first in (0, 1):
+            for f in frames:
+                f.out.zero_()
+            sb.stylize_batch(frames, 3, schedule={"persistent": persistent,
+                                                  "largest_first": largest_first})
+            torch.cuda.synchronize()
+            assert all(torch.equal(f.out, r) for f, r in zip(frames, ref))
+    # and one frame against the oracle
+    f0 = frames[0]
+    g0 = f0.tgt_guide.cpu().numpy().view(np.uint16)
+    out, _, _ = oracle.stylize(g0, src, style, 8, f0.levels, f0.threshold, 3, f0.seed)
+    assert np.array_equal(ref[0].cpu().numpy(), out)
