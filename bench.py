@@ -224,33 +224,35 @@ class ClockSampler:
 # CPU oracle baseline
 # ---------------------------------------------------------------------------
 
-def cpu_oracle_run(w, frames, steps: int = 0, warmup: int = 1, budget_s: float = 12.0):
+def cpu_oracle_run(w, frames, steps: int = 0, warmup: int = 1, budget_s: float = 12.0,
+                   threads: int = 0):
     """Times the oracle (assignment + RGBA8 vote, every host core) on bands of
     rows of the workload's frames.  Table entries a band needs are filled in
     untimed warm-up passes first (the GPU also runs with a resident table).
     steps > 0: `warmup` untimed then `steps` timed bands, the band height
     chosen so the timed part takes about `budget_s`; steps == 0: as many
-    64-row bands as fit in `budget_s`."""
+    64-row bands as fit in `budget_s`.  threads: oracle threads (0: every core)."""
     import oracle
     ex = w.exemplar
-    cores = os.cpu_count() or 1
+    all_cores = os.cpu_count() or 1
+    cores = threads or all_cores
     lut = oracle.new_lut(ex.guide.shape[2], ex.lut_bits)
     full = [np.ascontiguousarray(f) for f in frames[:2]]
 
     n_bands = 4  # a fixed set of bands: the warm-up fills every table entry they need
 
-    def run_band(k, rows):
+    def run_band(k, rows, n_threads=cores):
         g = full[k % len(full)]
         y0 = ((k % n_bands) * (g.shape[0] // n_bands)) % max(1, g.shape[0] - rows + 1)
         band = np.ascontiguousarray(g[y0:y0 + rows])
         t = time.perf_counter()
         a, _ = oracle.assign(band, ex.guide, ex.lut_bits, w.levels, w.threshold, w.seed + k % 2,
-                             lut=lut, n_threads=cores)
-        oracle.blend_rgba8(a, ex.style, w.blend_radius, n_threads=cores)
+                             lut=lut, n_threads=n_threads)
+        oracle.blend_rgba8(a, ex.style, w.blend_radius, n_threads=n_threads)
         return time.perf_counter() - t, band.shape[0] * band.shape[1]
 
     for k in range(max(n_bands, warmup)):  # untimed: fills the table entries bands need
-        run_band(k, 64)
+        run_band(k, 64, all_cores)
     t64, _ = run_band(0, 64)  # table resident now: time of one 64-row band
     rows = 64
     if steps > 0:
@@ -530,6 +532,12 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = cpu_oracle_run(w, frames)
         line["cpu_baseline"] = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        # one core: the kind of figure the paper quotes (seconds per frame on a
+        # single-core CPU), context only
+        r1 = cpu_oracle_run(w, frames, budget_s=6.0, threads=1)
+        line["cpu_baseline"]["single_core"] = {
+            "value": r1["value"], "unit": "Mpixel/s",
+            "s_per_frame": W * H / (r1["value"] * 1e6), "sample": r1["sample"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     lut.destroy()
