@@ -52,6 +52,7 @@ def _call_stylize(tgt, src, radius=2, levels=4, lut=None, style_wh=None):
     (_guide(64, 64, 3, 16), _guide(64, 64, 3, 16), -2),      # 16-bit x 3 unsupported
     (_guide(64, 64, 5, 8), _guide(64, 64, 5, 8), -1),        # 5 channels
     (_guide(64, 64, 3, 8), _guide(40000, 8, 3, 8), -1),      # source too wide
+    (_guide(65536, 2, 3, 8), _guide(64, 64, 3, 8), -1),      # target too wide
     (_guide(64, 64, 3, 8), _guide(0, 8, 3, 8), -1),          # empty source
     (_guide(64, 64, 3, 8), _guide(64, 64, 2, 8), -1),        # channel mismatch
     (_guide(64, 64, 3, 8, stride=10), _guide(64, 64, 3, 8), -1),   # short stride

@@ -313,3 +313,20 @@ def test_segmentation_guide_stylize_matches_oracle(cuda_device, radius, T):
     L = lev.cpu().numpy()
     seg = GS[A >> 16, A & 0xFFFF, 3]
     assert (seg[L > 1] == GT[..., 3][L > 1]).all()  # no chunk crosses a segment
+
+
+@pytest.mark.parametrize("tgt_shape,src_shape,levels", [
+    ((2, 65535), (3, 32767), 12),   # widest target and source the ABI allows
+    ((65535, 2), (32767, 3), 9),    # tallest
+])
+def test_maximum_target_and_source_sides(cuda_device, tgt_shape, src_shape, levels):
+    (Ht, Wt), (Hs, Ws) = tgt_shape, src_shape
+    tgt = synth.smooth_integer_guide(91, Ht, Wt, 3, step=7)
+    src = synth.smooth_integer_guide(92, Hs, Ws, 3, step=7)
+    style = synth.random_style(93, Hs, Ws)
+    c = dict(tgt=tgt, src=src, style=style, key_bits=5, levels=levels, threshold=400, radius=2,
+             seed=94)
+    lut, a, lev, out = _full(cuda_device, c)
+    ref_out, ref_a, ref_lev = oracle.stylize(tgt, src, style, 5, levels, 400, 2, 94)
+    assert np.array_equal(a, ref_a) and np.array_equal(lev, ref_lev)
+    assert np.array_equal(out, ref_out)
