@@ -330,3 +330,19 @@ def test_maximum_target_and_source_sides(cuda_device, tgt_shape, src_shape, leve
     ref_out, ref_a, ref_lev = oracle.stylize(tgt, src, style, 5, levels, 400, 2, 94)
     assert np.array_equal(a, ref_a) and np.array_equal(lev, ref_lev)
     assert np.array_equal(out, ref_out)
+
+
+@pytest.mark.parametrize("src_shape", [(1, 1), (1, 7), (5, 1), (2, 3)])
+def test_degenerate_tiny_sources(cuda_device, src_shape):
+    """A source of a pixel or a line: nearly every candidate falls outside it,
+    so level 1's clamp decides most pixels; the vote skips out-of-source taps."""
+    Hs, Ws = src_shape
+    tgt = synth.smooth_integer_guide(71, 45, 70, 3, step=5)
+    src = synth.random_guide(72, Hs, Ws, 3)
+    style = synth.random_style(73, Hs, Ws)
+    c = dict(tgt=tgt, src=src, style=style, key_bits=4, levels=4, threshold=5000, radius=2,
+             seed=74)
+    lut, a, lev, out = _full(cuda_device, c)
+    ref_out, ref_a, ref_lev = oracle.stylize(tgt, src, style, 4, 4, 5000, 2, 74)
+    assert np.array_equal(a, ref_a) and np.array_equal(lev, ref_lev)
+    assert np.array_equal(out, ref_out)
