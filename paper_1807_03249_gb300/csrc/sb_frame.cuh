@@ -643,7 +643,8 @@ __device__ __forceinline__ void vote_store(const FrameArgs &a, const Acc &acc, i
 // gathers per row) and compacts the pixels where some row has more breaks
 // (junctions of chunks, frame borders) into a second list; pass 2 sums those
 // tap by tap.  Every lane of a warp runs pass 1's loop the same number of
-// times (the compaction is warp-collective).
+// times.  Pass 1 reads the calling warp's own list (no block barrier before
+// it); pass 2 takes the block's complex pixels together (they are few).
 template <int R, bool F32>
 __device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const uint32_t *A,
                                                const uint32_t *E, const uint16_t *slow,
@@ -664,8 +665,9 @@ __device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const uint32_
         const uint32_t colr = ok ? __ldg(style32 + (vy * (uint32_t)sstride + vx)) : 0u;
         acc.add(colr, ok ? len : 0u);
     };
-    for (int j0 = 0; j0 < n_slow; j0 += kThreads) {
-        const int j = j0 + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    for (int j0 = 0; j0 < n_slow; j0 += 32) {
+        const int j = j0 + lane;
         const bool act = j < n_slow;
         const int k = act ? slow[j] : 0;
         const int tx = k % kTW, ty = k / kTW;
@@ -718,12 +720,15 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
     uint64_t *hu_row = reinterpret_cast<uint64_t *>(smem + L.off_masks);
     uint64_t *v_row = hu_row + RH;
     uint32_t *E_row = reinterpret_cast<uint32_t *>(v_row + RH);  // 4 words per region row
-    uint16_t *slow = reinterpret_cast<uint16_t *>(smem + L.off_list0);
-    int *slow_cnt = reinterpret_cast<int *>(smem + L.off_cnt) + 3;  // and the complex count
+    // each warp lists the pixels of its own output rows: 8 slots x 32 lanes
+    constexpr int kWarpList = kTH / kWarps * 2 * 32;
+    uint16_t *slow = reinterpret_cast<uint16_t *>(smem + L.off_list0) + warp * kWarpList;
+    uint16_t *cplx = reinterpret_cast<uint16_t *>(smem + L.off_list1);
+    int *cplx_cnt = reinterpret_cast<int *>(smem + L.off_cnt) + 3;
     const uint32_t *style32 = reinterpret_cast<const uint32_t *>(a.style);
     const int sstride = a.style_stride_px;
 
-    if (threadIdx.x < 2) slow_cnt[threadIdx.x] = 0;
+    if (threadIdx.x == 0) *cplx_cnt = 0;
     if constexpr (R > 0) {
         // per region row: E bit x <=> A[x] == A[x-1] + 1 (both valid);
         // hu bit tx <=> E bits tx+1 .. tx+2R all set (columns tx..tx+2R form
@@ -799,6 +804,8 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
             }
         }
     }
+    const unsigned lt = (1u << lane) - 1u;
+    int n_slow = 0;
 #pragma unroll
     for (int q = 0; q < kRowsPerWarp; ++q) {
         const int ty = warp + q * kWarps;
@@ -813,13 +820,13 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
                     a.rgba_out[(int64_t)(y0 + ty) * a.W + x0 + tx] = col[q][c];
                 }
             }
-            list_push(need[q][c], k, slow, slow_cnt);
+            const unsigned nm = __ballot_sync(0xFFFFFFFFu, need[q][c]);
+            if (need[q][c]) slow[n_slow + __popc(nm & lt)] = (uint16_t)k;
+            n_slow += __popc(nm);
         }
     }
-    __syncthreads();
-    vote_slow_list<R, F32>(a, A, E_row, slow, *slow_cnt,
-                           reinterpret_cast<uint16_t *>(smem + L.off_list1), slow_cnt + 1, x0,
-                           y0);
+    __syncwarp();
+    vote_slow_list<R, F32>(a, A, E_row, slow, n_slow, cplx, cplx_cnt, x0, y0);
 }
 
 // One 64 x 32 output tile (tile_x, tile_y) of one frame.
