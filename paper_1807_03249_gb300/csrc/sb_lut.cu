@@ -3,7 +3,9 @@
 // pixel with the nearest guide; Algorithm 2 calls this lookup for u*).
 //
 // The table is exact: bin k maps to argmin_u |rep(k) - G_S[u]|^2 with ties to
-// the smallest linear index.  Two kernels:
+// the smallest linear index.  8-bit guides keyed on at most three channels go
+// through a distance transform over the grid of guide values (edt_* below);
+// the others through a pruned search of two kernels:
 //   1. lut_tile_bounds: per 16x16 source tile, the per-channel min/max of the
 //      guide (an axis-aligned box in guide space).
 //   2. lut_search: one thread per bin, bins enumerated in Morton order so a
@@ -192,6 +194,74 @@ __global__ void __launch_bounds__(kLutThreads)
     if (valid) lut[idx] = (bl % (uint32_t)W) | ((bl / (uint32_t)W) << 16);
 }
 
+// ---------------------------------------------------------------------------
+// Distance-transform build for 8-bit guides keyed on at most three channels.
+// Over the 256^kc grid of keyed guide values, every value some source pixel
+// holds is a site carrying the smallest linear index of those pixels.  Three
+// separable passes (one per dimension) give each grid point its nearest site:
+// the squared distance and, on ties, the smallest index, in one 64-bit key
+// (distance << 32 | index), so each pass is a plain min.  The table reads the
+// grid at the bin representatives.  The separable decomposition of the
+// squared Euclidean distance makes the nested minima equal the minimum over
+// all sites, and every pass keeps the smallest index among equal distances,
+// so the entries equal the brute-force argmin (ties to the smallest index).
+constexpr uint64_t kEdtEmpty = (uint64_t)1 << 62;  // no site yet; + 255^2 << 32 cannot overflow
+
+__global__ void __launch_bounds__(256) edt_fill_kernel(uint64_t *__restrict__ grid, uint32_t n) {
+    const uint32_t i = blockIdx.x * 256u + threadIdx.x;
+    if (i < n) grid[i] = kEdtEmpty;
+}
+
+// Site of every source pixel: its keyed value (channels 0..kc-1, 8 bits each,
+// as packed) -> the smallest index holding it (distance 0).
+__global__ void __launch_bounds__(256) edt_sites_kernel(const uint32_t *__restrict__ packed,
+                                                       int64_t n_px, uint32_t key_mask,
+                                                       unsigned long long *__restrict__ grid) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i < n_px) atomicMin(&grid[__ldg(packed + i) & key_mask], (unsigned long long)i);
+}
+
+// One pass along the dimension of element stride `stride` (1, 256 or 65536):
+// CTA `line` holds the 256 grid points of one line, out[i] = min over j of
+// in[j] + ((i - j)^2 << 32).
+__global__ void __launch_bounds__(256) edt_pass_kernel(const uint64_t *__restrict__ in,
+                                                      uint64_t *__restrict__ out, int stride) {
+    __shared__ uint64_t line[256];
+    const int l = blockIdx.x;
+    const size_t base = (size_t)(l % stride) + (size_t)(l / stride) * (size_t)stride * 256;
+    const int i = threadIdx.x;
+    line[i] = in[base + (size_t)i * stride];
+    __syncthreads();
+    uint64_t best = kEdtEmpty << 1;
+#pragma unroll 8
+    for (int j = 0; j < 256; ++j) {
+        const uint32_t d = (uint32_t)(i - j) * (uint32_t)(i - j);
+        best = min(best, line[j] + ((uint64_t)d << 32));
+    }
+    out[base + (size_t)i * stride] = best;
+}
+
+// Table entry of bin g: the grid point at its representative.
+__global__ void __launch_bounds__(256) edt_extract_kernel(const uint64_t *__restrict__ grid,
+                                                         int kc, int key_bits, uint32_t n_bins,
+                                                         int W, uint32_t *__restrict__ lut) {
+    const uint32_t g = blockIdx.x * 256u + threadIdx.x;
+    if (g >= n_bins) return;
+    const int z = 8 - key_bits;
+    uint32_t voxel = 0;
+    for (int c = 0; c < kc; ++c) {
+        const uint32_t key = (g >> (c * key_bits)) & ((1u << key_bits) - 1u);
+        voxel |= ((key << z) + (((1u << z) - 1u) >> 1)) << (8 * c);
+    }
+    const uint32_t id = (uint32_t)(__ldg(grid + voxel) & 0xFFFFFFFFu);
+    lut[g] = (id % (uint32_t)W) | ((id / (uint32_t)W) << 16);
+}
+
+// Whether the distance-transform build applies (8-bit guides, at most three
+// keyed channels) and its scratch: two grids of 256^kc keys.
+__host__ inline bool edt_applies(int bits, int key_channels) { return bits == 8 && key_channels <= 3; }
+__host__ inline size_t edt_grid_points(int key_channels) { return (size_t)1 << (8 * key_channels); }
+
 struct LutLaunch {
     const sb_guide *src;
     int key_bits;
@@ -201,8 +271,29 @@ struct LutLaunch {
     uint32_t *entries;
     uint32_t *packed;   // NULL: search the caller's guide directly
     cudaStream_t stream;
+    uint64_t *edt = nullptr;  // two grids: the distance-transform build (needs packed)
     template <int C, int B>
     void operator()() {
+        if (edt && packed) {
+            const uint8_t *p = static_cast<const uint8_t *>(src->data);
+            const int64_t n_px = (int64_t)src->width * src->height;
+            const uint32_t n = (uint32_t)edt_grid_points(key_channels);
+            uint64_t *g0 = edt, *g1 = edt + n;
+            pack_guide_kernel<C, B><<<(unsigned)((n_px + 255) / 256), 256, 0, stream>>>(
+                p, src->row_stride, src->width, src->height, packed);
+            edt_fill_kernel<<<(n + 255) / 256, 256, 0, stream>>>(g0, n);
+            edt_sites_kernel<<<(unsigned)((n_px + 255) / 256), 256, 0, stream>>>(
+                packed, n_px, n - 1u, reinterpret_cast<unsigned long long *>(g0));
+            for (int d = 0; d < key_channels; ++d) {
+                edt_pass_kernel<<<n / 256, 256, 0, stream>>>(g0, g1, 1 << (8 * d));
+                uint64_t *t = g0;
+                g0 = g1;
+                g1 = t;
+            }
+            edt_extract_kernel<<<(n_bins + 255) / 256, 256, 0, stream>>>(
+                g0, key_channels, key_bits, n_bins, src->width, entries);
+            return;
+        }
         const int tiles_x = (src->width + kLutTile - 1) / kLutTile;
         const int tiles_y = (src->height + kLutTile - 1) / kLutTile;
         const int n_tiles = tiles_x * tiles_y;
@@ -268,18 +359,23 @@ extern "C" sb_status sb_build_lut_keyed(const sb_guide *src_guide, int32_t key_b
         delete lut;
         return cuda_fail(e, "sb_build_lut: packed guide allocation");
     }
-    uint4 *bounds = nullptr;
-    if ((e = cudaMallocAsync(&bounds, sizeof(uint4) * n_tiles, s)) != cudaSuccess) {
+    // scratch: tile bounds for the search, or two grids for the distance transform
+    const bool edt = edt_applies(src_guide->bits, key_channels);
+    void *scratch = nullptr;
+    const size_t scratch_bytes =
+        edt ? 2 * sizeof(uint64_t) * edt_grid_points(key_channels) : sizeof(uint4) * n_tiles;
+    if ((e = cudaMallocAsync(&scratch, scratch_bytes, s)) != cudaSuccess) {
         cudaFree(lut->entries);
         cudaFree(lut->src_packed);
         delete lut;
         return cuda_fail(e, "sb_build_lut: scratch allocation");
     }
-    LutLaunch L{src_guide, key_bits, key_channels, n_bins, bounds, lut->entries,
-                lut->src_packed, s};
+    LutLaunch L{src_guide, key_bits, key_channels, n_bins,
+                edt ? nullptr : static_cast<uint4 *>(scratch), lut->entries, lut->src_packed, s,
+                edt ? static_cast<uint64_t *>(scratch) : nullptr};
     dispatch_format(src_guide->channels, src_guide->bits, L);
     e = cudaGetLastError();
-    cudaFreeAsync(bounds, s);
+    cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(s);
         cudaFree(lut->entries);
