@@ -96,8 +96,10 @@ typedef struct sb_lut sb_lut;
  * channel to its top `key_bits` bits; bin k (channel keys concatenated,
  * channel 0 lowest) maps to the source pixel minimising the squared guide
  * distance to the bin representative rep_c = (key_c << z) + ((2^z - 1) >> 1),
- * z = bits - key_bits, ties to the smallest y * width + x.  The search is
- * exact (a pruned brute-force nearest-neighbour kernel).
+ * z = bits - key_bits, ties to the smallest y * width + x.  The result is
+ * exact either way it is computed: 8-bit guides keyed on at most three
+ * channels go through a distance transform over the grid of guide values,
+ * the others through a pruned brute-force nearest-neighbour kernel.
  *
  *   src_guide  source guide G_S (device).  The table refers to positions in
  *              it; later calls must pass a source guide of the same size and
@@ -106,7 +108,10 @@ typedef struct sb_lut sb_lut;
  *              channels * key_bits <= 24 (at most 16 Mi entries, 64 MiB).
  *   out        receives the new table; untouched on error.
  *   stream     the build is enqueued on this stream.  Temporary device
- *              memory is allocated and freed inside the call (stream-ordered).
+ *              memory is allocated and freed inside the call (stream-ordered):
+ *              2 * 8 * 256^kc bytes for the distance transform (268 MB for
+ *              three keyed channels), 16 bytes per 16x16 source tile for the
+ *              search.
  * Errors: SB_ERR_INVALID_ARG, SB_ERR_UNSUPPORTED, SB_ERR_OOM, SB_ERR_CUDA.
  */
 SB_API sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, sb_lut **out,
