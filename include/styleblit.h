@@ -132,7 +132,7 @@ SB_API sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, sb_lu
  *   table_out  device uint32[2^(channels * key_bits)], 4-byte aligned, owned by
  *              the caller: receives the same entries sb_build_lut computes.
  *   stream     the build is enqueued on this stream.
- * Scratch: a fixed 1 MiB array inside the library (file-scope device memory,
+ * Scratch: a fixed 1.1 MiB array inside the library (file-scope device memory,
  * held by every GPU that loads the library until the process exits).  The
  * first call on a device looks up that array's device address (once per
  * device, with the device current); make that first call before any stream

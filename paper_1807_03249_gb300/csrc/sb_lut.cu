@@ -86,6 +86,35 @@ __global__ void __launch_bounds__(256) lut_tile_bounds_kernel(const uint8_t *__r
     }
 }
 
+// Boxes of super-tiles (kSuper x kSuper tiles): the union of their tiles'
+// boxes, stored after the n_tiles tile boxes.
+constexpr int kSuper = 4;
+
+template <int C>
+__global__ void __launch_bounds__(256) lut_super_bounds_kernel(uint4 *__restrict__ bounds,
+                                                              int tiles_x, int tiles_y,
+                                                              int n_tiles, int supers_x,
+                                                              int n_supers) {
+    const int st = blockIdx.x * 256 + threadIdx.x;
+    if (st >= n_supers) return;
+    const int tx0 = (st % supers_x) * kSuper, ty0 = (st / supers_x) * kSuper;
+    uint32_t mn[4] = {0xFFFFu, 0xFFFFu, 0xFFFFu, 0xFFFFu}, mx[4] = {0, 0, 0, 0};
+    for (int ty = ty0; ty < min(ty0 + kSuper, tiles_y); ++ty)
+        for (int tx = tx0; tx < min(tx0 + kSuper, tiles_x); ++tx) {
+            const uint4 b = bounds[ty * tiles_x + tx];
+            const uint32_t w[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                mn[c] = min(mn[c], w[c] & 0xFFFFu);
+                mx[c] = max(mx[c], w[c] >> 16);
+            }
+        }
+    uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < C; ++c) w[c] = mn[c] | (mx[c] << 16);
+    bounds[n_tiles + st] = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 // squared distance from a representative to a tile's guide box
 template <int C, int B>
 __device__ __forceinline__ uint64_t box_distance(const uint32_t (&rep)[C], uint4 bb, int kc) {
@@ -143,9 +172,9 @@ __device__ __forceinline__ void scan_tile(const Reader &rd, int W, int H, int ti
 
 template <int C, int B, typename Reader>
 __global__ void __launch_bounds__(kLutThreads)
-    lut_search_kernel(const Reader rd, int W, int H, int tiles_x, int n_tiles,
-                      const uint4 *__restrict__ bounds, int key_bits, int kc, uint32_t n_bins,
-                      uint32_t *__restrict__ lut) {
+    lut_search_kernel(const Reader rd, int W, int H, int tiles_x, int n_tiles, int supers_x,
+                      int n_supers, const uint4 *__restrict__ bounds, int key_bits, int kc,
+                      uint32_t n_bins, uint32_t *__restrict__ lut) {
     const uint32_t g = blockIdx.x * kLutThreads + threadIdx.x;
     const bool valid = g < n_bins;
 
@@ -168,28 +197,52 @@ __global__ void __launch_bounds__(kLutThreads)
         idx |= key[c] << (c * key_bits);
     }
 
-    // pass A: the tile whose guide box is nearest
+    const int tiles_y = (n_tiles + tiles_x - 1) / tiles_x;
+    const uint4 *sup = bounds + n_tiles;  // super-tile boxes
+    // pass A: the super-tile whose box is nearest, then its nearest tile
     uint64_t best_lb = ~0ull;
-    int best_t = 0;
-    for (int t = 0; t < n_tiles; ++t) {
-        const uint64_t lb = box_distance<C, B>(rep, __ldg(&bounds[t]), kc);
+    int best_s = 0;
+    for (int st = 0; st < n_supers; ++st) {
+        const uint64_t lb = box_distance<C, B>(rep, __ldg(&sup[st]), kc);
         if (lb < best_lb) {
             best_lb = lb;
-            best_t = t;
+            best_s = st;
         }
     }
+    const int stx0 = (best_s % supers_x) * kSuper, sty0 = (best_s / supers_x) * kSuper;
+    int best_t = sty0 * tiles_x + stx0;
+    best_lb = ~0ull;
+    for (int ty = sty0; ty < min(sty0 + kSuper, tiles_y); ++ty)
+        for (int tx = stx0; tx < min(stx0 + kSuper, tiles_x); ++tx) {
+            const uint64_t lb = box_distance<C, B>(rep, __ldg(&bounds[ty * tiles_x + tx]), kc);
+            if (lb < best_lb) {
+                best_lb = lb;
+                best_t = ty * tiles_x + tx;
+            }
+        }
     // pass B: an initial best from that tile
     uint64_t bd = ~0ull;
     uint32_t bl = 0xFFFFFFFFu;
     scan_tile<C, B>(rd, W, H, tiles_x, best_t, rep_packed, kc, bd, bl);
-    // pass C: every tile that could still hold a better or tied-earlier pixel
-    for (int t = 0; t < n_tiles; ++t) {
-        const uint64_t lb = box_distance<C, B>(rep, __ldg(&bounds[t]), kc);
-        const uint32_t first = (uint32_t)((t / tiles_x) * kLutTile) * (uint32_t)W +
-                               (uint32_t)((t % tiles_x) * kLutTile);
-        const bool need = valid && (lb < bd || (lb == bd && first < bl));
-        if (__any_sync(0xFFFFFFFFu, need))
-            scan_tile<C, B>(rd, W, H, tiles_x, t, rep_packed, kc, bd, bl);
+    // pass C: every super-tile, then every tile of it, that could still hold a
+    // better or tied-earlier pixel (a tile's box lies in its super-tile's box
+    // and its first pixel comes no earlier than the super-tile's)
+    for (int st = 0; st < n_supers; ++st) {
+        const int tx0 = (st % supers_x) * kSuper, ty0 = (st / supers_x) * kSuper;
+        const uint64_t lbs = box_distance<C, B>(rep, __ldg(&sup[st]), kc);
+        const uint32_t first_s = (uint32_t)(ty0 * kLutTile) * (uint32_t)W + (uint32_t)(tx0 * kLutTile);
+        if (!__any_sync(0xFFFFFFFFu, valid && (lbs < bd || (lbs == bd && first_s < bl))))
+            continue;
+        for (int ty = ty0; ty < min(ty0 + kSuper, tiles_y); ++ty)
+            for (int tx = tx0; tx < min(tx0 + kSuper, tiles_x); ++tx) {
+                const int t = ty * tiles_x + tx;
+                const uint64_t lb = box_distance<C, B>(rep, __ldg(&bounds[t]), kc);
+                const uint32_t first = (uint32_t)(ty * kLutTile) * (uint32_t)W +
+                                       (uint32_t)(tx * kLutTile);
+                const bool need = valid && (lb < bd || (lb == bd && first < bl));
+                if (__any_sync(0xFFFFFFFFu, need))
+                    scan_tile<C, B>(rd, W, H, tiles_x, t, rep_packed, kc, bd, bl);
+            }
     }
     if (valid) lut[idx] = (bl % (uint32_t)W) | ((bl / (uint32_t)W) << 16);
 }
@@ -297,21 +350,25 @@ struct LutLaunch {
         const int tiles_x = (src->width + kLutTile - 1) / kLutTile;
         const int tiles_y = (src->height + kLutTile - 1) / kLutTile;
         const int n_tiles = tiles_x * tiles_y;
+        const int supers_x = (tiles_x + kSuper - 1) / kSuper;
+        const int n_supers = supers_x * ((tiles_y + kSuper - 1) / kSuper);
         const uint8_t *p = static_cast<const uint8_t *>(src->data);
         const int64_t n_px = (int64_t)src->width * src->height;
         const unsigned search_blocks = (n_bins + kLutThreads - 1) / kLutThreads;
         lut_tile_bounds_kernel<C, B><<<(n_tiles + 7) / 8, 256, 0, stream>>>(
             p, src->row_stride, src->width, src->height, tiles_x, n_tiles, bounds);
+        lut_super_bounds_kernel<C><<<(n_supers + 255) / 256, 256, 0, stream>>>(
+            bounds, tiles_x, tiles_y, n_tiles, supers_x, n_supers);
         if (packed) {
             pack_guide_kernel<C, B><<<(unsigned)((n_px + 255) / 256), 256, 0, stream>>>(
                 p, src->row_stride, src->width, src->height, packed);
             lut_search_kernel<C, B><<<search_blocks, kLutThreads, 0, stream>>>(
                 PackedReader{packed, src->width}, src->width, src->height, tiles_x, n_tiles,
-                bounds, key_bits, key_channels, n_bins, entries);
+                supers_x, n_supers, bounds, key_bits, key_channels, n_bins, entries);
         } else {
             lut_search_kernel<C, B><<<search_blocks, kLutThreads, 0, stream>>>(
                 RawReader<C, B>{p, src->row_stride}, src->width, src->height, tiles_x, n_tiles,
-                bounds, key_bits, key_channels, n_bins, entries);
+                supers_x, n_supers, bounds, key_bits, key_channels, n_bins, entries);
         }
     }
 };
@@ -363,7 +420,9 @@ extern "C" sb_status sb_build_lut_keyed(const sb_guide *src_guide, int32_t key_b
     const bool edt = edt_applies(src_guide->bits, key_channels);
     void *scratch = nullptr;
     const size_t scratch_bytes =
-        edt ? 2 * sizeof(uint64_t) * edt_grid_points(key_channels) : sizeof(uint4) * n_tiles;
+        edt ? 2 * sizeof(uint64_t) * edt_grid_points(key_channels)
+            : sizeof(uint4) * (n_tiles + (size_t)((tiles_x + kSuper - 1) / kSuper) *
+                                             ((tiles_y + kSuper - 1) / kSuper));
     if ((e = cudaMallocAsync(&scratch, scratch_bytes, s)) != cudaSuccess) {
         cudaFree(lut->entries);
         cudaFree(lut->src_packed);
@@ -429,7 +488,7 @@ extern "C" sb_status sb_lut_info(const sb_lut *lut, const uint32_t **entries, in
 // allocator already owns the device's memory, or a frame loop that must not
 // call cudaMalloc (it can synchronise the device and fail under memory
 // pressure).  sb_build_lut_noalloc builds the same table into a buffer the
-// caller provides.  Its only scratch, the per-tile guide boxes, lives in the
+// caller provides.  Its only scratch, the tile and super-tile guide boxes, lives in the
 // fixed array below, which every GPU that loads this library holds until the
 // process exits; the search reads the caller's guide directly instead of a
 // packed copy.
@@ -437,7 +496,8 @@ extern "C" sb_status sb_lut_info(const sb_lut *lut, const uint32_t **entries, in
 namespace sb {
 
 constexpr int kStaticBoundsTiles = 65536;  // 1 MiB: 16x16 tiles of a 4096 x 4096 source
-static __device__ __align__(256) uint4 g_static_bounds[kStaticBoundsTiles];
+constexpr int kStaticSupers = 5376;        // their super-tiles, any aspect (sides <= 32767)
+static __device__ __align__(256) uint4 g_static_bounds[kStaticBoundsTiles + kStaticSupers];
 
 // Device address of g_static_bounds on the current device, looked up once per
 // device (host code cannot use the symbol itself as a device pointer).
@@ -477,7 +537,8 @@ extern "C" sb_status sb_build_lut_noalloc(const sb_guide *src_guide, int32_t key
         return fail(SB_ERR_INVALID_ARG, "table_out: NULL or not 4-byte aligned");
     const int tiles_x = (src_guide->width + kLutTile - 1) / kLutTile;
     const int tiles_y = (src_guide->height + kLutTile - 1) / kLutTile;
-    if ((int64_t)tiles_x * tiles_y > kStaticBoundsTiles)
+    const int64_t n_supers = (int64_t)((tiles_x + kSuper - 1) / kSuper) * ((tiles_y + kSuper - 1) / kSuper);
+    if ((int64_t)tiles_x * tiles_y > kStaticBoundsTiles || n_supers > kStaticSupers)
         return fail(SB_ERR_INVALID_ARG,
                     "sb_build_lut_noalloc: source guide too large for the fixed scratch "
                     "(at most 65536 tiles of 16x16 pixels, e.g. 4096 x 4096)");
