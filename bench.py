@@ -112,10 +112,13 @@ def algorithmic_bytes(w, frame) -> dict:
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources the profiled batch kernel is compiled from (the
+    frame kernels' header, the shared device helpers and the per-format
+    translation units), so committed counters go stale when it changes."""
     d = os.path.join(ROOT, "paper_1807_03249_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
+        if f in ("sb_frame.cuh", "sb_internal.cuh") or (f.startswith("sb_frame_c") and f.endswith(".cu")):
             h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
