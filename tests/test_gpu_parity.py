@@ -37,7 +37,8 @@ def _full(dev, c, radius=None):
 
 @pytest.mark.parametrize("channels,bits,key_bits,shape", [
     (3, 8, 4, (37, 45)), (2, 8, 6, (64, 64)), (1, 8, 8, (17, 9)), (4, 8, 3, (33, 20)),
-    (2, 16, 7, (48, 40)), (1, 16, 10, (30, 31)), (3, 8, 5, (1, 1)), (2, 8, 8, (70, 3))])
+    (2, 16, 7, (48, 40)), (1, 16, 10, (30, 31)), (3, 8, 5, (1, 1)), (2, 8, 8, (70, 3)),
+    (3, 8, 8, (5, 7))])  # 2^24 bins: every guide value its own bin
 def test_lut_all_entries_match_oracle(cuda_device, channels, bits, key_bits, shape):
     H, W = shape
     src = synth.random_guide(1000 + channels * 7 + bits, H, W, channels, bits=bits)
