@@ -258,7 +258,8 @@ __global__ void __launch_bounds__(kLutThreads)
 // squared Euclidean distance makes the nested minima equal the minimum over
 // all sites, and every pass keeps the smallest index among equal distances,
 // so the entries equal the brute-force argmin (ties to the smallest index).
-constexpr uint64_t kEdtEmpty = (uint64_t)1 << 62;  // no site yet; + 255^2 << 32 cannot overflow
+// no site yet: above every real key; adding three passes' (255^2 << 32) stays below 2^63
+constexpr uint64_t kEdtEmpty = (uint64_t)1 << 62;
 
 __global__ void __launch_bounds__(256) edt_fill_kernel(uint64_t *__restrict__ grid, uint32_t n) {
     const uint32_t i = blockIdx.x * 256u + threadIdx.x;
