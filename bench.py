@@ -590,8 +590,25 @@ def workload_stats(sb, g_tgt, g_src, lut, w, radius: int, n_sample: int = 20000,
         xx = np.clip(px[k] + offs, 0, W - 1)
         win = d[np.ix_(np.unique(yy), np.unique(xx))]
         counts[k] = len(np.unique(win))
+    # texture coherence: share of horizontally adjacent pixels whose source
+    # positions are adjacent too, for StyleBlit and for the lookup-only
+    # comparator (its source map read back through a style that holds each
+    # texel's own coordinates)
+    Hs, Ws = g_src.shape[:2]
+    yy, xx = np.mgrid[0:Hs, 0:Ws]
+    coord = np.stack([xx & 0xFF, xx >> 8, yy & 0xFF, yy >> 8], axis=-1).astype(np.uint8)
+    lk = sb.lookup_only(g_tgt, g_src, torch.from_numpy(coord).to(g_tgt.device), lut)
+    torch.cuda.synchronize()
+    lkc = lk.cpu().numpy().astype(np.int64)
+    lx, ly = lkc[..., 0] | (lkc[..., 1] << 8), lkc[..., 2] | (lkc[..., 3] << 8)
+
+    def coherent(sx, sy):
+        return float(((sx[:, 1:] == sx[:, :-1] + 1) & (sy[:, 1:] == sy[:, :-1])).mean())
+
     return {"level_histogram": {f"L{l + 1}": int(c) for l, c in enumerate(hist)},
             "mean_accepted_level": float((np.arange(1, w.levels + 1) * hist).sum() / hist.sum()),
+            "source_coherence": {"stylize": coherent(a & 0xFFFF, a >> 16),
+                                 "lookup_only": coherent(lx, ly)},
             "mean_distinct_translations_per_window": float(counts.mean()),
             "windows_with_several_translations": float((counts > 1).mean()),
             "sample": f"frame 0, {n_sample} pixels for the window statistics (window clipped "
