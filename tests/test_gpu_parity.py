@@ -347,3 +347,70 @@ def test_degenerate_tiny_sources(cuda_device, src_shape):
     ref_out, ref_a, ref_lev = oracle.stylize(tgt, src, style, 4, 4, 5000, 2, 74)
     assert np.array_equal(a, ref_a) and np.array_equal(lev, ref_lev)
     assert np.array_equal(out, ref_out)
+
+
+def _random_case(seed):
+    """A seeded random configuration: guide format, sizes, key bits and keyed
+    channels, levels, threshold, blend radius, jitter seed."""
+    rng = np.random.default_rng(seed)
+    channels, bits = [(1, 8), (2, 8), (3, 8), (4, 8), (1, 16), (2, 16)][seed % 6]
+    kc = int(rng.integers(1, channels + 1))
+    kb_max = min(bits, 24 // kc, 12)
+    kb = int(rng.integers(max(1, kb_max - 4), kb_max + 1))
+    Ht, Wt = int(rng.integers(1, 140)), int(rng.integers(1, 200))
+    Hs, Ws = int(rng.integers(1, 60)), int(rng.integers(1, 60))
+    high = (1 << bits) - 1
+    tgt = synth.random_guide(10 * seed + 1, Ht, Wt, channels, bits=bits, low=0,
+                             high=int(rng.integers(1, high + 1)))
+    src = synth.random_guide(10 * seed + 2, Hs, Ws, channels, bits=bits, low=0,
+                             high=int(rng.integers(1, high + 1)))
+    style = synth.random_style(10 * seed + 3, Hs, Ws)
+    T = int(rng.choice([0, int(rng.integers(0, 4 * high * high)), (1 << 64) - 1]))
+    return dict(tgt=tgt, src=src, style=style, kb=kb, kc=kc, levels=int(rng.integers(1, 10)),
+                T=T, r=int(rng.integers(0, 8)), seed=int(rng.integers(0, 2**32)))
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_randomized_configurations_match_oracle(cuda_device, seed):
+    """Seeded random formats, sizes (ragged, tiny), key bits and keyed channels,
+    level counts, thresholds and radii: table, assignment, levels and RGBA8
+    output equal the oracle's."""
+    c = _random_case(seed)
+    gt, gs, st = to_dev(c["tgt"], cuda_device), to_dev(c["src"], cuda_device), to_dev(c["style"], cuda_device)
+    lut = sb.build_lut(gs, c["kb"], key_channels=c["kc"])
+    a, lev = sb.assign_chunks(gt, gs, lut, c["levels"], c["T"], c["seed"])
+    out = sb.stylize(gt, gs, st, lut, c["levels"], c["T"], c["r"], c["seed"])
+    torch.cuda.synchronize()
+    ref_lut = oracle.build_lut(c["src"], c["kb"], key_channels=c["kc"])
+    assert np.array_equal(lut.entries().cpu().numpy().view(np.uint32), ref_lut)
+    ref_out, ref_a, ref_lev = oracle.stylize(c["tgt"], c["src"], c["style"], c["kb"], c["levels"],
+                                             c["T"], c["r"], c["seed"], key_channels=c["kc"])
+    assert np.array_equal(u32(a), ref_a) and np.array_equal(lev.cpu().numpy(), ref_lev)
+    assert np.array_equal(out.cpu().numpy(), ref_out)
+
+
+@pytest.mark.parametrize("fmt", range(6))
+def test_randomized_mixed_batches_match_oracle(cuda_device, fmt):
+    """Four random frames of one guide format, each with its own exemplar, key
+    bits, keyed channels, levels, threshold and seed, in one batch under every
+    launch schedule: each output equals the oracle's."""
+    cases = [_random_case(fmt + 6 * j) for j in range(4)]
+    radius = cases[0]["r"]
+    luts, frames, refs = [], [], []
+    for c in cases:
+        lut = sb.build_lut(to_dev(c["src"], cuda_device), c["kb"], key_channels=c["kc"])
+        luts.append(lut)
+        frames.append((to_dev(c["tgt"], cuda_device), lut, to_dev(c["style"], cuda_device),
+                       c["levels"], c["T"], c["seed"]))
+        refs.append(oracle.stylize(c["tgt"], c["src"], c["style"], c["kb"], c["levels"], c["T"],
+                                   radius, c["seed"], key_channels=c["kc"])[0])
+    for persistent in (0, 1):
+        for largest_first in (0, 1):
+            outs = sb.stylize_batch([sb.BatchFrame(*f) for f in frames], radius,
+                                    schedule={"persistent": persistent,
+                                              "largest_first": largest_first})
+            torch.cuda.synchronize()
+            for k, (o, r) in enumerate(zip(outs, refs)):
+                assert np.array_equal(o.cpu().numpy(), r), f"schedule {persistent}{largest_first} frame {k}"
+    for lut in luts:
+        lut.destroy()
