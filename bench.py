@@ -720,6 +720,8 @@ def run_served(dev, n_requests: int = 10000, rate_hz: float = 2000.0, pool: int 
         return Request(i, float(arrivals[i] - t0), int(exs[i]), guides[i % pool], 6, 300,
                        int(seeds[i]), out=outs[i % pool])
 
+    # slot arenas sized for the largest possible group before anything is timed
+    srv.reserve(sum(sorted(srv.device_bytes(g) for g in guides)[-srv.sched.max_batch:]))
     warm = [make(i, arrivals[0]) for i in range(64)]
     srv.run(warm, real_time=False)
     reqs = [make(i, arrivals[0]) for i in range(n_requests)]

@@ -9,6 +9,12 @@ admitted group runs as one sb_stylize_batch launch between its host-to-device
 and device-to-host copies on its slot's stream, so groups on different slots
 overlap on the device, and requests arriving meanwhile join the next group.
 
+Each slot owns one device buffer (its arena) that holds its group's guides and
+outputs, so serving makes no device allocation per request: an arena grows in
+64 MiB steps only when a group larger than any before arrives on that slot, and
+`Server.reserve` sizes them before serving starts.  The byte budget bounds the
+bytes of the requests in flight.
+
 The scheduling core (`Scheduler`) is plain Python and knows nothing of CUDA;
 `Server` binds it to the library.  Every result is exactly what sb_stylize
 gives for that request alone (the batch kernel is bit-identical per frame).
@@ -17,6 +23,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import time
 from typing import Callable
 
@@ -102,8 +109,36 @@ class Server:
         self.radius = radius
         self.sched = Scheduler(budget_bytes, slots, min(max_batch, MAX_BATCH))
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
+        # per slot: one device buffer that holds its group's guides and outputs
+        self.arenas = [None] * slots
         self.exemplars = {}
-        self.inflight = []  # (event, slot, group, keep-alive tensors)
+        self.inflight = []  # (event, slot, group)
+
+    _ALIGN = 256
+
+    @classmethod
+    def _aligned(cls, n: int) -> int:
+        return (n + cls._ALIGN - 1) // cls._ALIGN * cls._ALIGN
+
+    _ARENA_STEP = 64 << 20
+
+    def _ensure_arena(self, slot: int, nbytes: int):
+        # Grows in 64 MiB steps to the largest group the slot has held.  Only
+        # called while the slot is free: its previous group's work has completed.
+        buf = self.arenas[slot]
+        if buf is not None and buf.numel() >= nbytes:
+            return buf
+        cap = max(1, -(-nbytes // self._ARENA_STEP)) * self._ARENA_STEP
+        self.arenas[slot] = None
+        buf = self.torch.empty(cap, dtype=self.torch.uint8, device=self.device)
+        self.arenas[slot] = buf
+        return buf
+
+    def reserve(self, nbytes_per_slot: int):
+        """Sizes every slot's arena for groups of up to nbytes_per_slot bytes
+        now, so that serving allocates no device memory afterwards."""
+        for slot in self.sched.free_slots:
+            self._ensure_arena(slot, nbytes_per_slot)
 
     def add_exemplar(self, ex_id: int, guide, style, key_bits: int):
         """Uploads an exemplar and builds its table; both stay resident."""
@@ -115,8 +150,10 @@ class Server:
         self.exemplars[ex_id] = (gd, sd, build_lut(gd, key_bits))
 
     def device_bytes(self, guide) -> int:
+        """Device bytes of one request in its slot's arena: the guide and the
+        RGBA8 output, each 256-byte aligned."""
         h, w = int(guide.shape[0]), int(guide.shape[1])
-        return guide.element_size() * guide.numel() + 4 * h * w
+        return self._aligned(guide.element_size() * guide.numel()) + self._aligned(4 * h * w)
 
     def submit(self, req: Request):
         req.nbytes = self.device_bytes(req.guide)
@@ -126,33 +163,48 @@ class Server:
         from . import BatchFrame, stylize_batch
         t = self.torch
         s = self.streams[slot]
-        keep = []
+        arena = self._ensure_arena(slot, sum(r.nbytes for r in group))
+        typed = {}
+        off = 0
+
+        def carve(nbytes: int, dtype, shape):
+            # a contiguous [H, W, C] view at the next 256-byte boundary
+            nonlocal off
+            if dtype not in typed:
+                typed[dtype] = arena.view(dtype)
+            a = typed[dtype]
+            size = a.element_size()
+            v = a.as_strided(shape, (shape[1] * shape[2], shape[2], 1), off // size)
+            off += self._aligned(nbytes)
+            return v
+
         with t.cuda.stream(s):
             frames = []
             for r in group:
-                g = t.empty(r.guide.shape, dtype=r.guide.dtype, device=self.device)
+                h, w = int(r.guide.shape[0]), int(r.guide.shape[1])
+                g = carve(r.guide.element_size() * r.guide.numel(), r.guide.dtype,
+                          r.guide.shape)
                 g.copy_(r.guide, non_blocking=True)
+                o = carve(4 * h * w, t.uint8, (h, w, 4))
                 _, sd, lut = self.exemplars[r.exemplar]
-                frames.append(BatchFrame(g, lut, sd, r.levels, r.threshold, r.seed))
-                keep.append(g)
+                frames.append(BatchFrame(g, lut, sd, r.levels, r.threshold, r.seed, out=o))
             stylize_batch(frames, self.radius, stream=s)
             for r, f in zip(group, frames):
                 if r.out is None:
                     r.out = t.empty(f.out.shape, dtype=t.uint8, pin_memory=True)
                 r.out.copy_(f.out, non_blocking=True)
-                keep.append(f.out)
             ev = t.cuda.Event()
             ev.record(s)
         t_adm = now()
         for r in group:
             r.admitted = t_adm
-        self.inflight.append((ev, slot, group, keep))
+        self.inflight.append((ev, slot, group))
 
     def poll(self, now: Callable[[], float]):
         """Retires finished groups (frees their slot and bytes); returns their requests."""
         done, still = [], []
         for item in self.inflight:
-            ev, slot, group, keep = item
+            ev, slot, group = item
             if ev.query():
                 t_done = now()
                 for r in group:
@@ -174,22 +226,32 @@ class Server:
 
     def run(self, requests, real_time: bool = True, timeout_s: float = 600.0):
         """Feeds requests at their arrival times (seconds from the start) and
-        serves them all; returns the finished requests in completion order."""
+        serves them all; returns the finished requests in completion order.
+        The cyclic garbage collector is paused while the loop runs (after one
+        collection before it), so no collection pass lands inside a request's
+        latency."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         finished = []
-        t0 = time.perf_counter()
-        now = lambda: time.perf_counter() - t0  # noqa: E731
-        n = len(pending)
-        while len(finished) < n:
-            t = now()
-            if t > timeout_s:
-                raise TimeoutError(f"served {len(finished)} of {n} requests in {timeout_s} s")
-            while pending and (not real_time or pending[0].arrival <= t):
-                r = pending.popleft()
-                if not real_time:
-                    r.arrival = t
-                self.submit(r)
-            finished.extend(self.poll(now))
-            self.pump(now)
-        self.torch.cuda.synchronize(self.device)
-        return finished, now()
+        gc_was_enabled = gc.isenabled()
+        gc.collect()
+        gc.disable()
+        try:
+            t0 = time.perf_counter()
+            now = lambda: time.perf_counter() - t0  # noqa: E731
+            n = len(pending)
+            while len(finished) < n:
+                t = now()
+                if t > timeout_s:
+                    raise TimeoutError(f"served {len(finished)} of {n} requests in {timeout_s} s")
+                while pending and (not real_time or pending[0].arrival <= t):
+                    r = pending.popleft()
+                    if not real_time:
+                        r.arrival = t
+                    self.submit(r)
+                finished.extend(self.poll(now))
+                self.pump(now)
+            self.torch.cuda.synchronize(self.device)
+            return finished, now()
+        finally:
+            if gc_was_enabled:
+                gc.enable()

@@ -38,3 +38,32 @@ def test_served_results_equal_each_request_alone(cuda_device):
         torch.cuda.synchronize()
         assert torch.equal(r.out, alone.cpu()), f"request {r.rid}"
         assert r.done >= r.admitted >= r.arrival
+
+
+def test_reserved_server_allocates_no_device_memory_while_serving(cuda_device):
+    """After Server.reserve, serving a stream of mixed sizes makes no device
+    allocation (guides and outputs live in the slot arenas) and every result
+    still equals the request alone."""
+    rng = np.random.default_rng(9)
+    srv = Server(cuda_device, radius=2, budget_bytes=1 << 30, slots=3, max_batch=4)
+    g = synth.sphere_normals(128)
+    st = synth.value_noise_style(9, 128, 128, octaves=3, base_cell=16)
+    srv.add_exemplar(0, g, st, key_bits=5)
+    reqs = []
+    for i in range(24):
+        w, h = int(rng.integers(1, 500)), int(rng.integers(1, 300))
+        gi = torch.from_numpy(synth.bump_normals(900 + i, h, w, 4, (5.0, 40.0))).pin_memory()
+        reqs.append(Request(i, 0.0, 0, gi, 5, 300, int(rng.integers(0, 2**32)),
+                            out=torch.empty((h, w, 4), dtype=torch.uint8).pin_memory()))
+    srv.reserve(sum(sorted(srv.device_bytes(r.guide) for r in reqs)[-4:]))
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_stats(cuda_device)["allocation.all.allocated"]
+    done, _ = srv.run(reqs, real_time=False)
+    after = torch.cuda.memory_stats(cuda_device)["allocation.all.allocated"]
+    assert len(done) == len(reqs) and after == before
+    _, sd, lut = srv.exemplars[0]
+    gd = srv.exemplars[0][0]
+    for r in reqs:
+        alone = sb.stylize(r.guide.to(cuda_device), gd, sd, lut, 5, 300, 2, r.seed)
+        torch.cuda.synchronize()
+        assert torch.equal(r.out, alone.cpu()), f"request {r.rid}"
