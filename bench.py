@@ -486,6 +486,7 @@ def run_gpu(args):
     e2e_value = job_throughput(world, px_step, args.e2e_steps, ms_e2e)
     h2d = sum(f.nbytes for f in frames)
     d2h = sum(o.numel() for o in host_out)
+    copy_ceiling = copies_only(dev, host_in, host_out, staging, e2e_streams, stream)
 
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
@@ -534,7 +535,12 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                     "api": f"stylize_batch_host (pinned host in/out), groups of {E2E_GROUP} "
-                           "frames over 3 streams"},
+                           "frames over 3 streams",
+                    "copies_only": {
+                        "value": job_throughput(world, px_step, 1, copy_ceiling["ms"]),
+                        "unit": "Mpixel/s", "gbs": (h2d + d2h) / copy_ceiling["ms"] / 1e6,
+                        "what": "the same step's host-to-device and device-to-host copies "
+                                "alone, same streams (the host link's ceiling for e2e)"}},
             "issue_roofline": issue,
             "per_frame_launch": per_frame,
             "lookup_only": lookup,
@@ -561,6 +567,42 @@ def run_gpu(args):
     lut.destroy()
     if world > 1:
         dist.destroy_process_group()
+
+
+def copies_only(dev, host_in, host_out, staging, streams, main, reps: int = 10) -> dict:
+    """Times one e2e step's copies without the kernels: every guide in and
+    every output out through the staging buffers, groups over the same
+    streams.  The result bounds what any e2e step can reach on this host link."""
+    import torch
+
+    bufs = list(staging.values())
+    assert len(bufs) == len(host_in)
+
+    def step():
+        for g0 in range(0, len(bufs), E2E_GROUP):
+            st = streams[(g0 // E2E_GROUP) % len(streams)]
+            with torch.cuda.stream(st):
+                for k in range(g0, min(len(bufs), g0 + E2E_GROUP)):
+                    bufs[k][0].copy_(host_in[k], non_blocking=True)
+                    host_out[k].copy_(bufs[k][1], non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(main):
+        t0.record(main)
+    for st in streams:
+        st.wait_event(t0)
+    for _ in range(reps):
+        step()
+    for st in streams:
+        ev = torch.cuda.Event()
+        ev.record(st)
+        main.wait_event(ev)
+    with torch.cuda.stream(main):
+        t1.record(main)
+    torch.cuda.synchronize()
+    return {"ms": t0.elapsed_time(t1) / reps}
 
 
 def workload_stats(sb, g_tgt, g_src, lut, w, radius: int, n_sample: int = 20000,
