@@ -418,8 +418,15 @@ def run_gpu(args):
     ms_pf = time_graph(graph_frames, pf_steps)
 
     # the lookup-only comparator (Section 4, texture mapping) on the same frames:
-    # one short launch per frame, spread over four streams (forked from and
-    # joined back to the step's stream) so their ramps and tails overlap
+    # one short launch per frame spread over four streams (forked from and
+    # joined back to the step's stream) so their ramps and tails overlap; beside
+    # it, one sb_lookup_only_batch launch per step
+    lk_frames = [sb.BatchFrame(g_tgt[i], lut, style, w.levels, w.threshold, 0, out=outs[i])
+                 for i in range(FRAMES_PER_STEP)]
+
+    def step_lookup_batch():
+        sb.lookup_only_batch(lk_frames)
+
     lk_streams = [torch.cuda.Stream(dev) for _ in range(4)]
 
     def step_lookup():
@@ -436,15 +443,19 @@ def run_gpu(args):
             join.record(st_)
             cur.wait_event(join)
 
-    graph_lookup = capture(step_lookup)
-    ms_lk = time_graph(graph_lookup, pf_steps)
     lk_bytes = FRAMES_PER_STEP * ab["frame_bytes"]
-    lookup = {"value": job_throughput(world, px_step, pf_steps, ms_lk), "unit": "Mpixel/s",
-              "ms_per_step": ms_lk / pf_steps,
-              "hbm_frac": lk_bytes / (ms_lk / pf_steps / 1e3) / 1e9 /
-              (measured_peaks().get("hbm_gbs") or 6800.0),
-              "what": "C_T[p] = C_S[LUT(G_T[p])] per pixel, one lookup_kernel per frame, "
-                      "frames over 4 streams"}
+    hbm_peak = measured_peaks().get("hbm_gbs") or 6800.0
+
+    def lookup_line(ms):
+        return {"value": job_throughput(world, px_step, pf_steps, ms), "unit": "Mpixel/s",
+                "ms_per_step": ms / pf_steps,
+                "hbm_frac": lk_bytes / (ms / pf_steps / 1e3) / 1e9 / hbm_peak}
+
+    lookup = lookup_line(time_graph(capture(step_lookup), pf_steps))
+    lookup["what"] = ("C_T[p] = C_S[LUT(G_T[p])] per pixel, one sb_lookup_only launch per frame "
+                      "over 4 streams")
+    lookup["batched"] = lookup_line(time_graph(capture(step_lookup_batch), pf_steps))
+    lookup["batched"]["what"] = "every frame of the step in one sb_lookup_only_batch launch"
     per_frame = {"value": job_throughput(world, px_step, pf_steps, ms_pf), "unit": "Mpixel/s",
                  "ms_per_step": ms_pf / pf_steps, "steps": pf_steps,
                  "launch": "CUDA graph of frames_per_step sb_stylize kernels (one per frame)"}
@@ -734,7 +745,9 @@ def run_served(dev, n_requests: int = 10000, rate_hz: float = 2000.0, pool: int 
                seed: int = 5000) -> dict:
     """The served workload: a seeded Poisson stream of stylisation requests,
     frame sizes log-uniform in [256^2, 3840x2160], 16 resident 1024^2
-    exemplars, 40 GB admission budget, 5x5 blend, L=6, T=300.  Request guides
+    exemplars, 40 GB admission budget, 5x5 blend, L=6, T=300, served three
+    times (each pass's p50/p99 and longest host-loop gap are reported; the
+    headline is the pass with the median p99).  Request guides
     are crops of one generated 3840x2160 normal field held in a pool of pinned
     buffers (outputs of the same pool entry are overwritten; they are not
     checked here -- tests/test_gpu_serve.py checks served results)."""
@@ -766,9 +779,18 @@ def run_served(dev, n_requests: int = 10000, rate_hz: float = 2000.0, pool: int 
     srv.reserve(sum(sorted(srv.device_bytes(g) for g in guides)[-srv.sched.max_batch:]))
     warm = [make(i, arrivals[0]) for i in range(64)]
     srv.run(warm, real_time=False)
-    reqs = [make(i, arrivals[0]) for i in range(n_requests)]
-    done, wall = srv.run(reqs, real_time=True)
-    out = latency_summary(done, wall)
+    # three independent passes over the same arrival stream; the headline is
+    # the pass with the median p99 (a single host stall moves one pass's p99)
+    runs = []
+    for _ in range(3):
+        reqs = [make(i, arrivals[0]) for i in range(n_requests)]
+        done, wall = srv.run(reqs, real_time=True)
+        r = latency_summary(done, wall)
+        r["max_loop_gap_ms"] = srv.max_loop_gap_s * 1e3
+        runs.append(r)
+    out = dict(sorted(runs, key=lambda r: r["p99_ms"])[1])
+    out["runs"] = [{k: r[k] for k in ("p50_ms", "p99_ms", "mean_ms", "max_loop_gap_ms")}
+                   for r in runs]
 
     # saturation: the same kind of requests all waiting at once, served by the
     # continuous-batching loop vs one plain sb_stylize per request (with the

@@ -318,6 +318,24 @@ SB_API sb_status sb_lookup_only(const sb_guide *tgt_guide, const sb_guide *src_g
                                 const sb_rgba8 *src_style, const sb_lut *lut, uint8_t *rgba8_out,
                                 sb_stream stream);
 
+/*
+ * sb_lookup_only_batch -- sb_lookup_only for many frames in a single launch
+ * (the comparator of Section 4, batched like sb_stylize_batch).  Frames may
+ * differ in size and exemplar and share the guide format.  Every frame's
+ * output is bit-identical to sb_lookup_only on that frame alone.
+ *
+ *   frames     host array of n_frames descriptors (sb_frame; only tgt_guide,
+ *              lut, src_style and rgba8_out are used: levels, threshold and
+ *              seed are ignored).  Read during the call; the device data
+ *              must stay valid until the stream reaches the launch.
+ *   n_frames   0..128 (0 is a no-op).
+ * Allocates nothing.  Errors: SB_ERR_INVALID_ARG (a frame's arguments, as for
+ * sb_lookup_only; the message names the frame), SB_ERR_UNSUPPORTED (frames
+ * with different guide formats), SB_ERR_CUDA.
+ */
+SB_API sb_status sb_lookup_only_batch(const sb_frame *frames, int32_t n_frames,
+                                      sb_stream stream);
+
 /* Static description of a status code. */
 SB_API const char *sb_status_string(sb_status status);
 

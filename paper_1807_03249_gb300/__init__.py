@@ -26,7 +26,8 @@ import torch
 from . import _build
 
 __all__ = ["StyleBlitError", "Lut", "build_lut", "assign_chunks", "blend", "stylize",
-           "stylize_batch", "autotune_batch", "BatchFrame", "lookup_only", "stylize_host",
+           "stylize_batch", "autotune_batch", "BatchFrame", "lookup_only", "lookup_only_batch",
+           "stylize_host",
            "stylize_batch_host",
            "library_path", "load_library",
            "EXPORTED_SYMBOLS", "version", "MAX_BATCH"]
@@ -40,6 +41,7 @@ _STATUS = {0: "SB_OK", -1: "SB_ERR_INVALID_ARG", -2: "SB_ERR_UNSUPPORTED", -3: "
 EXPORTED_SYMBOLS = ["sb_build_lut", "sb_build_lut_keyed", "sb_build_lut_noalloc", "sb_lut_destroy", "sb_lut_info",
                     "sb_assign_chunks", "sb_blend", "sb_stylize", "sb_stylize_batch",
                     "sb_stylize_batch_sched", "sb_autotune_batch", "sb_lookup_only",
+                    "sb_lookup_only_batch",
                     "sb_status_string", "sb_last_error", "sb_version"]
 
 
@@ -106,6 +108,7 @@ def load_library(build_if_missing: bool = True):
             "sb_stylize": (ctypes.c_int, [P(_Guide), P(_Guide), P(_Rgba8), vp, i32, u64, i32,
                                           u32, vp, vp]),
             "sb_stylize_batch": (ctypes.c_int, [P(_Frame), i32, i32, vp]),
+            "sb_lookup_only_batch": (ctypes.c_int, [P(_Frame), i32, vp]),
             "sb_stylize_batch_sched": (ctypes.c_int, [P(_Frame), i32, i32, P(_Schedule), vp]),
             "sb_autotune_batch": (ctypes.c_int, [P(_Frame), i32, i32, i32, P(_Schedule),
                                                  P(ctypes.c_float), vp]),
@@ -340,6 +343,17 @@ def stylize_batch(frames, radius: int, stream=None, schedule: dict | None = None
         _check("sb_stylize_batch_sched",
                lib.sb_stylize_batch_sched(arr, len(frames), radius, ctypes.byref(sc),
                                           _stream(stream)))
+    return [f.out for f in frames]
+
+
+def lookup_only_batch(frames, stream=None):
+    """The lookup-only comparator (Section 4) for up to MAX_BATCH frames
+    (BatchFrame; their levels, threshold and seed are ignored) in one launch;
+    returns their outputs.  Frames share the guide format."""
+    lib = load_library()
+    frames = list(frames)
+    arr = _frames_array(frames)
+    _check("sb_lookup_only_batch", lib.sb_lookup_only_batch(arr, len(frames), _stream(stream)))
     return [f.out for f in frames]
 
 

@@ -234,6 +234,7 @@ static sb_status prepare_batch(const sb_frame *frames, int32_t n_frames, int32_t
         if ((st = check_style(&f.src_style, name)) != SB_OK) return st;
         if (f.src_style.width != f.lut->src_w || f.src_style.height != f.lut->src_h)
             return fail(SB_ERR_INVALID_ARG, std::string(name) + ": size differs from the lut's guide");
+        std::snprintf(name, sizeof name, "frames[%d]", k);
         if (f.levels < 1 || f.levels > kMaxLevels)
             return fail(SB_ERR_INVALID_ARG, std::string(name) + ": levels must be in [1, 12]");
         const int64_t npx = (int64_t)f.tgt_guide.width * f.tgt_guide.height;

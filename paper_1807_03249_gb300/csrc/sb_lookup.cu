@@ -3,7 +3,12 @@
 // target pixel copies the style at the table entry of its own guide,
 // C_T[p] = C_S[LUT(G_T[p])].  Four neighbouring pixels per thread, 1024 per
 // CTA along a row, so guide reads and output stores are coalesced vectors and
-// the table and style gathers (small, L2-resident) overlap.
+// the table and style gathers (small, L2-resident) overlap.  sb_lookup_only_batch
+// maps many frames in one launch.
+#include <climits>
+#include <cstdio>
+#include <string>
+
 #include "sb_internal.cuh"
 
 namespace sb {
@@ -47,25 +52,31 @@ __host__ inline int lookup_vec_align(int channels, int bits) {
     return bytes4 == 12 ? 4 : bytes4;
 }
 
-// Four pixels per thread.  With vec (guide rows aligned for load4, output
-// rows 16-byte aligned, W a multiple of 4) a thread reads its four guide
-// values with one to three vector loads and writes one 16-byte store; the
-// four table and style gathers of a thread are independent, so they overlap.
+// One frame of the lookup: its target guide, table, style and output.
+struct LookupFrame {
+    const uint8_t *tgt;
+    int64_t tgt_stride;
+    const uint32_t *lut;
+    const uint32_t *style;
+    uint32_t *out;
+    int W, H, key_bits, key_channels, style_stride_px;
+    int vec;  // guide rows aligned for load4, output 16-byte aligned, W % 4 == 0
+};
+
+// Four pixels per thread, pixels [x, x + 4) of row y with x = (bx * 256 + thread)
+// * 4.  With vec a thread reads its four guide values with one to three vector
+// loads and writes one 16-byte store; the four table and style gathers of a
+// thread are independent, so they overlap.
 template <int C, int B>
-__global__ void __launch_bounds__(kLookupThreads)
-    lookup_kernel(const uint8_t *__restrict__ tgt, int64_t tgt_stride, int W,
-                  const uint32_t *__restrict__ lut, int key_bits, int key_channels,
-                  const uint32_t *__restrict__ style, int64_t style_stride_px,
-                  uint32_t *__restrict__ out, bool vec) {
+__device__ __forceinline__ void lookup_chunk(const LookupFrame &f, int bx, int y) {
     using F = GuideFmt<C, B>;
-    const int x = (blockIdx.x * kLookupThreads + threadIdx.x) * kLookupPx;
-    const int y = blockIdx.y;
-    if (x >= W) return;
-    const uint8_t *row = tgt + (int64_t)y * tgt_stride;
-    uint32_t *orow = out + (int64_t)y * W;
+    const int x = (bx * kLookupThreads + (int)threadIdx.x) * kLookupPx;
+    if (x >= f.W) return;
+    const uint8_t *row = f.tgt + (int64_t)y * f.tgt_stride;
+    uint32_t *orow = f.out + (int64_t)y * f.W;
     uint32_t g[kLookupPx];
-    const int n = min(kLookupPx, W - x);
-    if (vec) {
+    const int n = min(kLookupPx, f.W - x);
+    if (f.vec) {
         load4<C, B>(row, x, g);
     } else {
 #pragma unroll
@@ -74,18 +85,67 @@ __global__ void __launch_bounds__(kLookupThreads)
     uint32_t u[kLookupPx], c[kLookupPx];
 #pragma unroll
     for (int k = 0; k < kLookupPx; ++k)
-        u[k] = k < n ? __ldg(lut + F::key(g[k], key_bits, key_channels)) : 0u;
+        u[k] = k < n ? __ldg(f.lut + F::key(g[k], f.key_bits, f.key_channels)) : 0u;
 #pragma unroll
     for (int k = 0; k < kLookupPx; ++k)
-        c[k] = k < n ? __ldg(style + (int64_t)(u[k] >> 16) * style_stride_px + (u[k] & 0xFFFFu))
+        c[k] = k < n ? __ldg(f.style + (int64_t)(u[k] >> 16) * f.style_stride_px +
+                             (u[k] & 0xFFFFu))
                      : 0u;
-    if (vec) {
+    if (f.vec) {
         *reinterpret_cast<uint4 *>(orow + x) = make_uint4(c[0], c[1], c[2], c[3]);
     } else {
 #pragma unroll
         for (int k = 0; k < kLookupPx; ++k)
             if (k < n) orow[x + k] = c[k];
     }
+}
+
+template <int C, int B>
+__global__ void __launch_bounds__(kLookupThreads) lookup_kernel(const LookupFrame f) {
+    lookup_chunk<C, B>(f, blockIdx.x, blockIdx.y);
+}
+
+// Many frames in one launch: block (t, k) maps row chunk t of frame k (the
+// grid is as wide as the largest frame's chunk count; blocks past a smaller
+// frame's end return at once).  Small frames then fill the GPU together
+// instead of one short launch each, and no block searches for its frame.
+constexpr int kMaxLookupBatch = 128;
+struct LookupBatch {
+    int n;
+    int blocks[kMaxLookupBatch];    // row chunks of frame k (0 without pixels)
+    int blocks_x[kMaxLookupBatch];  // chunks per row
+    LookupFrame f[kMaxLookupBatch];
+};
+
+template <int C, int B>
+__global__ void __launch_bounds__(kLookupThreads)
+    lookup_batch_kernel(const __grid_constant__ LookupBatch b) {
+    const int k = blockIdx.y, t = blockIdx.x;
+    if (t >= b.blocks[k]) return;
+    lookup_chunk<C, B>(b.f[k], t % b.blocks_x[k], t / b.blocks_x[k]);
+}
+
+constexpr int kPxPerLookupBlock = kLookupThreads * kLookupPx;
+
+// The launch descriptor of one frame (guide format C, B).
+template <int C, int B>
+LookupFrame lookup_frame(const sb_guide *tgt, const sb_lut *lut, const sb_rgba8 *style,
+                         uint32_t *out) {
+    const int al = lookup_vec_align(C, B);
+    LookupFrame f;
+    f.tgt = static_cast<const uint8_t *>(tgt->data);
+    f.tgt_stride = tgt->row_stride;
+    f.lut = lut->entries;
+    f.style = reinterpret_cast<const uint32_t *>(style->data);
+    f.out = out;
+    f.W = tgt->width;
+    f.H = tgt->height;
+    f.key_bits = lut->key_bits;
+    f.key_channels = lut->key_channels;
+    f.style_stride_px = (int)(style->row_stride / 4);
+    f.vec = tgt->width % 4 == 0 && (uintptr_t)tgt->data % al == 0 && tgt->row_stride % al == 0 &&
+            (uintptr_t)out % 16 == 0;
+    return f;
 }
 
 struct LookupLaunch {
@@ -96,15 +156,25 @@ struct LookupLaunch {
     cudaStream_t s;
     template <int C, int B>
     void operator()() {
-        const int al = lookup_vec_align(C, B);
-        const bool vec = tgt->width % 4 == 0 && (uintptr_t)tgt->data % al == 0 &&
-                         tgt->row_stride % al == 0 && (uintptr_t)out % 16 == 0;
-        constexpr int kPxPerBlock = kLookupThreads * kLookupPx;
-        const dim3 grid((tgt->width + kPxPerBlock - 1) / kPxPerBlock, tgt->height);
-        lookup_kernel<C, B><<<grid, kLookupThreads, 0, s>>>(
-            static_cast<const uint8_t *>(tgt->data), tgt->row_stride, tgt->width, lut->entries,
-            lut->key_bits, lut->key_channels, reinterpret_cast<const uint32_t *>(style->data),
-            style->row_stride / 4, out, vec);
+        const dim3 grid((tgt->width + kPxPerLookupBlock - 1) / kPxPerLookupBlock, tgt->height);
+        lookup_kernel<C, B><<<grid, kLookupThreads, 0, s>>>(lookup_frame<C, B>(tgt, lut, style, out));
+    }
+};
+
+struct LookupBatchLaunch {
+    const sb_frame *frames;
+    LookupBatch *b;
+    cudaStream_t s;
+    template <int C, int B>
+    void operator()() {
+        for (int k = 0; k < b->n; ++k)
+            b->f[k] = lookup_frame<C, B>(&frames[k].tgt_guide, frames[k].lut,
+                                         &frames[k].src_style,
+                                         reinterpret_cast<uint32_t *>(frames[k].rgba8_out));
+        int width = 0;
+        for (int k = 0; k < b->n; ++k) width = max(width, b->blocks[k]);
+        if (width > 0)
+            lookup_batch_kernel<C, B><<<dim3(width, b->n), kLookupThreads, 0, s>>>(*b);
     }
 };
 
@@ -139,5 +209,54 @@ extern "C" sb_status sb_lookup_only(const sb_guide *tgt_guide, const sb_guide *s
                    static_cast<cudaStream_t>(stream)};
     dispatch_format(tgt_guide->channels, tgt_guide->bits, L);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "sb_lookup_only");
+    return ok();
+}
+
+extern "C" sb_status sb_lookup_only_batch(const sb_frame *frames, int32_t n_frames,
+                                          sb_stream stream) {
+    if (n_frames < 0 || n_frames > kMaxLookupBatch)
+        return fail(SB_ERR_INVALID_ARG, "n_frames must be in [0, 128]");
+    if (n_frames == 0) return ok();
+    if (!frames) return fail(SB_ERR_INVALID_ARG, "frames: NULL");
+    static thread_local LookupBatch b;  // ~9 KB: kept off the stack
+    const int channels = frames[0].tgt_guide.channels, bits = frames[0].tgt_guide.bits;
+    char name[64];
+    b.n = n_frames;
+    for (int k = 0; k < n_frames; ++k) {
+        const sb_frame &f = frames[k];
+        std::snprintf(name, sizeof name, "frames[%d].tgt_guide", k);
+        sb_status st = check_guide(&f.tgt_guide, name, false);
+        if (st != SB_OK) return st;
+        if (f.tgt_guide.channels != channels || f.tgt_guide.bits != bits)
+            return fail(SB_ERR_UNSUPPORTED,
+                        "sb_lookup_only_batch: frames must share one guide format");
+        std::snprintf(name, sizeof name, "frames[%d]", k);
+        if (!f.lut) return fail(SB_ERR_INVALID_ARG, std::string(name) + ": lut NULL");
+        if (f.lut->channels != channels || f.lut->bits != bits)
+            return fail(SB_ERR_INVALID_ARG, std::string(name) + ": lut built for another format");
+        std::snprintf(name, sizeof name, "frames[%d].src_style", k);
+        if ((st = check_style(&f.src_style, name)) != SB_OK) return st;
+        if (f.src_style.width != f.lut->src_w || f.src_style.height != f.lut->src_h)
+            return fail(SB_ERR_INVALID_ARG, std::string(name) + ": size differs from the lut's guide");
+        std::snprintf(name, sizeof name, "frames[%d]", k);
+        const int64_t npx = (int64_t)f.tgt_guide.width * f.tgt_guide.height;
+        if (npx > 0 && (!f.rgba8_out || ((uintptr_t)f.rgba8_out % 4)))
+            return fail(SB_ERR_INVALID_ARG, std::string(name) + ": rgba8_out NULL or misaligned");
+        const int64_t bx = (f.tgt_guide.width + kPxPerLookupBlock - 1) / kPxPerLookupBlock;
+        const int64_t blocks = npx > 0 ? bx * f.tgt_guide.height : 0;
+        if (blocks > INT_MAX) return fail(SB_ERR_INVALID_ARG, std::string(name) + ": too many blocks");
+        b.blocks[k] = (int)blocks;
+        b.blocks_x[k] = bx > 1 ? (int)bx : 1;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (int k = 0; k < n_frames; ++k)
+        if (frames[k].lut->device != dev) return fail(SB_ERR_INVALID_ARG, "a lut lives on another device");
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pending CUDA error");
+    LookupBatchLaunch L{frames, &b, static_cast<cudaStream_t>(stream)};
+    if (!dispatch_format(channels, bits, L))
+        return fail(SB_ERR_UNSUPPORTED, "unsupported guide format");
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "sb_lookup_only_batch");
     return ok();
 }

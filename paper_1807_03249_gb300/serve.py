@@ -113,6 +113,7 @@ class Server:
         self.arenas = [None] * slots
         self.exemplars = {}
         self.inflight = []  # (event, slot, group)
+        self.max_loop_gap_s = 0.0
 
     _ALIGN = 256
 
@@ -229,7 +230,9 @@ class Server:
         serves them all; returns the finished requests in completion order.
         The cyclic garbage collector is paused while the loop runs (after one
         collection before it), so no collection pass lands inside a request's
-        latency."""
+        latency.  `max_loop_gap_s` records the longest time between two
+        passes of the loop: a stall of the host side (the process not
+        running, or a blocking call) shows there."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         finished = []
         gc_was_enabled = gc.isenabled()
@@ -239,8 +242,12 @@ class Server:
             t0 = time.perf_counter()
             now = lambda: time.perf_counter() - t0  # noqa: E731
             n = len(pending)
+            self.max_loop_gap_s = 0.0
+            t_prev = 0.0
             while len(finished) < n:
                 t = now()
+                self.max_loop_gap_s = max(self.max_loop_gap_s, t - t_prev)
+                t_prev = t
                 if t > timeout_s:
                     raise TimeoutError(f"served {len(finished)} of {n} requests in {timeout_s} s")
                 while pending and (not real_time or pending[0].arrival <= t):

@@ -100,6 +100,12 @@ def test_invalid_batch_and_schedule_arguments_are_rejected_on_the_host():
     assert lib.sb_autotune_batch(frames, 1, 2, 3, None, ctypes.byref(ms), None) == -1  # no best
     assert lib.sb_autotune_batch(frames, 1, 2, 0, ctypes.byref(best), None, None) == -1  # reps
     assert b"reps" in lib.sb_last_error()
+    assert lib.sb_lookup_only_batch(frames, 129, None) == -1           # too many frames
+    assert lib.sb_lookup_only_batch(None, 1, None) == -1               # NULL frames
+    assert lib.sb_lookup_only_batch(frames, -1, None) == -1
+    assert lib.sb_lookup_only_batch(frames, 0, None) == 0              # empty batch: no-op
+    assert lib.sb_lookup_only_batch(frames, 1, None) == -1             # frame 0 has no guide
+    assert b"frames[0]" in lib.sb_last_error()
 
 
 def test_style_too_large_for_32_bit_offsets_is_rejected():

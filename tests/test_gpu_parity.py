@@ -414,3 +414,34 @@ def test_randomized_mixed_batches_match_oracle(cuda_device, fmt):
                 assert np.array_equal(o.cpu().numpy(), r), f"schedule {persistent}{largest_first} frame {k}"
     for lut in luts:
         lut.destroy()
+
+
+@pytest.mark.parametrize("channels,bits", [(3, 8), (2, 16), (1, 8)])
+def test_lookup_only_batch_matches_oracle_and_single_calls(cuda_device, channels, bits):
+    """sb_lookup_only_batch: frames of mixed sizes (ragged widths, a row offset
+    for the per-pixel path, an empty frame in the middle) over two exemplars
+    in one launch; each output equals the oracle's and the single-frame call's."""
+    high = (1 << bits) - 1
+    exs = []
+    for e in range(2):
+        src = synth.random_guide(50 + e, 23 + e, 31 + 2 * e, channels, bits=bits, high=high)
+        style = synth.random_style(60 + e, 23 + e, 31 + 2 * e)
+        gs = to_dev(src, cuda_device)
+        exs.append((src, style, gs, to_dev(style, cuda_device), sb.build_lut(gs, 5)))
+    shapes = [(37, 1030, 0), (5, 1028, 0), (0, 64, 0), (64, 2051, 1), (1, 1, 0), (33, 260, 0)]
+    frames, refs, singles = [], [], []
+    for i, (h, w, off) in enumerate(shapes):
+        src, style, gs, st, lut = exs[i % 2]
+        big = synth.random_guide(70 + i, h, w + off, channels, bits=bits, high=high)
+        gt = to_dev(big, cuda_device)[:, off:]
+        tgt = np.ascontiguousarray(big[:, off:])
+        frames.append(sb.BatchFrame(gt, lut, st, 1, 0, 0))
+        refs.append(oracle.lookup_only(tgt, src, style, 5))
+        singles.append(sb.lookup_only(gt, gs, st, lut))
+    outs = sb.lookup_only_batch(frames)
+    torch.cuda.synchronize()
+    for k, (o, r, s1) in enumerate(zip(outs, refs, singles)):
+        assert np.array_equal(o.cpu().numpy(), r), f"frame {k}"
+        assert torch.equal(o, s1), f"frame {k}"
+    for e in exs:
+        e[4].destroy()
