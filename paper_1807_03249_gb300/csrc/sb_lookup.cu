@@ -1,9 +1,9 @@
 // Lookup-only comparator (Section 4: texture mapping and The Lit Sphere map
 // every target pixel through its own guide value, without chunks): each
 // target pixel copies the style at the table entry of its own guide,
-// C_T[p] = C_S[LUT(G_T[p])].  Four neighbouring pixels per thread, 1024 per
-// CTA along a row, so guide reads and output stores are coalesced vectors and
-// the table and style gathers (small, L2-resident) overlap.  sb_lookup_only_batch
+// C_T[p] = C_S[LUT(G_T[p])].  Four or eight neighbouring pixels per thread
+// along a row, so guide reads and output stores are coalesced vectors and the
+// table and style gathers (small, L2-resident) overlap.  sb_lookup_only_batch
 // maps many frames in one launch.
 #include <climits>
 #include <cstdio>
@@ -14,7 +14,6 @@
 namespace sb {
 
 constexpr int kLookupThreads = 256;
-constexpr int kLookupPx = 4;  // pixels per thread (one vector load of guide, one store)
 
 // The packed guide values of pixels x .. x+3 of a row whose start is aligned to
 // the vector width (x a multiple of 4): one to three aligned loads.
@@ -63,47 +62,68 @@ struct LookupFrame {
     int vec;  // guide rows aligned for load4, output 16-byte aligned, W % 4 == 0
 };
 
-// Four pixels per thread, pixels [x, x + 4) of row y with x = (bx * 256 + thread)
-// * 4.  With vec a thread reads its four guide values with one to three vector
-// loads and writes one 16-byte store; the four table and style gathers of a
-// thread are independent, so they overlap.
-template <int C, int B>
+// Q quads of four pixels per thread, pixels [x, x + 4Q) of row y with x = (bx *
+// 256 + thread) * 4Q.  With vec a thread reads each quad's guide values with
+// one to three vector loads and writes one 16-byte store per quad; all guide
+// loads are issued first, then the table and style gathers of every pixel,
+// which are independent, so they overlap.  Two quads per thread keep more bytes
+// in flight on wide rows; rows narrower than 2048 pixels use one (a second quad
+// would leave most of a row's only block idle).
+template <int C, int B, int Q>
 __device__ __forceinline__ void lookup_chunk(const LookupFrame &f, int bx, int y) {
     using F = GuideFmt<C, B>;
-    const int x = (bx * kLookupThreads + (int)threadIdx.x) * kLookupPx;
+    constexpr int P = 4 * Q;
+    const int x = (bx * kLookupThreads + (int)threadIdx.x) * P;
     if (x >= f.W) return;
     const uint8_t *row = f.tgt + (int64_t)y * f.tgt_stride;
     uint32_t *orow = f.out + (int64_t)y * f.W;
-    uint32_t g[kLookupPx];
-    const int n = min(kLookupPx, f.W - x);
+    const int n = min(P, f.W - x);
+    uint32_t g[Q][4];
     if (f.vec) {
-        load4<C, B>(row, x, g);
+        // W % 4 == 0: every quad is whole or absent
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if (4 * q < n) {
+                load4<C, B>(row, x + 4 * q, g[q]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) g[q][k] = 0u;
+            }
+        }
     } else {
 #pragma unroll
-        for (int k = 0; k < kLookupPx; ++k) g[k] = k < n ? F::load(row, 0, x + k, 0) : 0u;
+        for (int k = 0; k < P; ++k) g[k / 4][k % 4] = k < n ? F::load(row, 0, x + k, 0) : 0u;
     }
-    uint32_t u[kLookupPx], c[kLookupPx];
+    uint32_t u[P], c[P];
 #pragma unroll
-    for (int k = 0; k < kLookupPx; ++k)
-        u[k] = k < n ? __ldg(f.lut + F::key(g[k], f.key_bits, f.key_channels)) : 0u;
+    for (int k = 0; k < P; ++k)
+        u[k] = k < n ? __ldg(f.lut + F::key(g[k / 4][k % 4], f.key_bits, f.key_channels)) : 0u;
 #pragma unroll
-    for (int k = 0; k < kLookupPx; ++k)
+    for (int k = 0; k < P; ++k)
         c[k] = k < n ? __ldg(f.style + (int64_t)(u[k] >> 16) * f.style_stride_px +
                              (u[k] & 0xFFFFu))
                      : 0u;
     if (f.vec) {
-        *reinterpret_cast<uint4 *>(orow + x) = make_uint4(c[0], c[1], c[2], c[3]);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+            if (4 * q < n)
+                *reinterpret_cast<uint4 *>(orow + x + 4 * q) =
+                    make_uint4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
     } else {
 #pragma unroll
-        for (int k = 0; k < kLookupPx; ++k)
+        for (int k = 0; k < P; ++k)
             if (k < n) orow[x + k] = c[k];
     }
 }
 
-template <int C, int B>
+template <int C, int B, int Q>
 __global__ void __launch_bounds__(kLookupThreads) lookup_kernel(const LookupFrame f) {
-    lookup_chunk<C, B>(f, blockIdx.x, blockIdx.y);
+    lookup_chunk<C, B, Q>(f, blockIdx.x, blockIdx.y);
 }
+
+// Quads per thread for rows of width w, and pixels per block.
+__host__ inline int lookup_quads(int w) { return w >= 2048 ? 2 : 1; }
+__host__ inline int lookup_px_per_block(int quads) { return kLookupThreads * 4 * quads; }
 
 // Many frames in one launch: block (t, k) maps row chunk t of frame k (the
 // grid is as wide as the largest frame's chunk count; blocks past a smaller
@@ -117,15 +137,13 @@ struct LookupBatch {
     LookupFrame f[kMaxLookupBatch];
 };
 
-template <int C, int B>
+template <int C, int B, int Q>
 __global__ void __launch_bounds__(kLookupThreads)
     lookup_batch_kernel(const __grid_constant__ LookupBatch b) {
     const int k = blockIdx.y, t = blockIdx.x;
     if (t >= b.blocks[k]) return;
-    lookup_chunk<C, B>(b.f[k], t % b.blocks_x[k], t / b.blocks_x[k]);
+    lookup_chunk<C, B, Q>(b.f[k], t % b.blocks_x[k], t / b.blocks_x[k]);
 }
-
-constexpr int kPxPerLookupBlock = kLookupThreads * kLookupPx;
 
 // The launch descriptor of one frame (guide format C, B).
 template <int C, int B>
@@ -156,14 +174,18 @@ struct LookupLaunch {
     cudaStream_t s;
     template <int C, int B>
     void operator()() {
-        const dim3 grid((tgt->width + kPxPerLookupBlock - 1) / kPxPerLookupBlock, tgt->height);
-        lookup_kernel<C, B><<<grid, kLookupThreads, 0, s>>>(lookup_frame<C, B>(tgt, lut, style, out));
+        const int q = lookup_quads(tgt->width), px = lookup_px_per_block(q);
+        const dim3 grid((tgt->width + px - 1) / px, tgt->height);
+        const LookupFrame f = lookup_frame<C, B>(tgt, lut, style, out);
+        if (q == 2) lookup_kernel<C, B, 2><<<grid, kLookupThreads, 0, s>>>(f);
+        else lookup_kernel<C, B, 1><<<grid, kLookupThreads, 0, s>>>(f);
     }
 };
 
 struct LookupBatchLaunch {
     const sb_frame *frames;
     LookupBatch *b;
+    int quads;
     cudaStream_t s;
     template <int C, int B>
     void operator()() {
@@ -173,8 +195,9 @@ struct LookupBatchLaunch {
                                          reinterpret_cast<uint32_t *>(frames[k].rgba8_out));
         int width = 0;
         for (int k = 0; k < b->n; ++k) width = max(width, b->blocks[k]);
-        if (width > 0)
-            lookup_batch_kernel<C, B><<<dim3(width, b->n), kLookupThreads, 0, s>>>(*b);
+        if (width == 0) return;
+        if (quads == 2) lookup_batch_kernel<C, B, 2><<<dim3(width, b->n), kLookupThreads, 0, s>>>(*b);
+        else lookup_batch_kernel<C, B, 1><<<dim3(width, b->n), kLookupThreads, 0, s>>>(*b);
     }
 };
 
@@ -222,6 +245,12 @@ extern "C" sb_status sb_lookup_only_batch(const sb_frame *frames, int32_t n_fram
     const int channels = frames[0].tgt_guide.channels, bits = frames[0].tgt_guide.bits;
     char name[64];
     b.n = n_frames;
+    // two quads per thread only when every frame's rows are wide enough
+    int quads = 2;
+    for (int k = 0; k < n_frames; ++k)
+        if ((int64_t)frames[k].tgt_guide.width * frames[k].tgt_guide.height > 0)
+            quads = min(quads, lookup_quads(frames[k].tgt_guide.width));
+    const int px_per_block = lookup_px_per_block(quads);
     for (int k = 0; k < n_frames; ++k) {
         const sb_frame &f = frames[k];
         std::snprintf(name, sizeof name, "frames[%d].tgt_guide", k);
@@ -242,7 +271,7 @@ extern "C" sb_status sb_lookup_only_batch(const sb_frame *frames, int32_t n_fram
         const int64_t npx = (int64_t)f.tgt_guide.width * f.tgt_guide.height;
         if (npx > 0 && (!f.rgba8_out || ((uintptr_t)f.rgba8_out % 4)))
             return fail(SB_ERR_INVALID_ARG, std::string(name) + ": rgba8_out NULL or misaligned");
-        const int64_t bx = (f.tgt_guide.width + kPxPerLookupBlock - 1) / kPxPerLookupBlock;
+        const int64_t bx = ((int64_t)f.tgt_guide.width + px_per_block - 1) / px_per_block;
         const int64_t blocks = npx > 0 ? bx * f.tgt_guide.height : 0;
         if (blocks > INT_MAX) return fail(SB_ERR_INVALID_ARG, std::string(name) + ": too many blocks");
         b.blocks[k] = (int)blocks;
@@ -254,7 +283,7 @@ extern "C" sb_status sb_lookup_only_batch(const sb_frame *frames, int32_t n_fram
         if (frames[k].lut->device != dev) return fail(SB_ERR_INVALID_ARG, "a lut lives on another device");
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) return cuda_fail(e, "pending CUDA error");
-    LookupBatchLaunch L{frames, &b, static_cast<cudaStream_t>(stream)};
+    LookupBatchLaunch L{frames, &b, quads, static_cast<cudaStream_t>(stream)};
     if (!dispatch_format(channels, bits, L))
         return fail(SB_ERR_UNSUPPORTED, "unsupported guide format");
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "sb_lookup_only_batch");

@@ -249,7 +249,10 @@ def test_lookup_only_matches_oracle(cuda_device, case):
     (1028, 5, 3, 0),   # four pixels per thread with vector loads; two CTAs per row
     (1030, 7, 3, 0),   # width not a multiple of 4: per-pixel loads
     (515, 3, 2, 1),    # rows start one pixel in: unaligned
-    (260, 4, 4, 0), (261, 3, 1, 0)])
+    (260, 4, 4, 0), (261, 3, 1, 0),
+    (2052, 3, 3, 0),   # rows >= 2048: two quads per thread, the last thread has one
+    (2051, 2, 3, 0),   # two quads per thread, per-pixel loads
+    (4096, 2, 4, 0)])
 def test_lookup_only_vector_and_ragged_rows(cuda_device, W, H, channels, offset):
     """The comparator's vector path (aligned rows, width a multiple of 4) and
     its per-pixel path give the same pixels as the oracle."""
@@ -416,8 +419,9 @@ def test_randomized_mixed_batches_match_oracle(cuda_device, fmt):
         lut.destroy()
 
 
+@pytest.mark.parametrize("wide", [False, True])
 @pytest.mark.parametrize("channels,bits", [(3, 8), (2, 16), (1, 8)])
-def test_lookup_only_batch_matches_oracle_and_single_calls(cuda_device, channels, bits):
+def test_lookup_only_batch_matches_oracle_and_single_calls(cuda_device, channels, bits, wide):
     """sb_lookup_only_batch: frames of mixed sizes (ragged widths, a row offset
     for the per-pixel path, an empty frame in the middle) over two exemplars
     in one launch; each output equals the oracle's and the single-frame call's."""
@@ -429,6 +433,8 @@ def test_lookup_only_batch_matches_oracle_and_single_calls(cuda_device, channels
         gs = to_dev(src, cuda_device)
         exs.append((src, style, gs, to_dev(style, cuda_device), sb.build_lut(gs, 5)))
     shapes = [(37, 1030, 0), (5, 1028, 0), (0, 64, 0), (64, 2051, 1), (1, 1, 0), (33, 260, 0)]
+    if wide:  # every frame at least 2048 pixels wide: two quads per thread
+        shapes = [(3, 2052, 0), (0, 4096, 0), (2, 4100, 1), (1, 2048, 0)]
     frames, refs, singles = [], [], []
     for i, (h, w, off) in enumerate(shapes):
         src, style, gs, st, lut = exs[i % 2]
