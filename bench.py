@@ -55,8 +55,9 @@ def _args():
     p.add_argument("--no-uneven", action="store_true",
                    help="skip the uneven batch (64 mixed-size frames, 8 exemplars)")
     p.add_argument("--profile-once", action="store_true",
-                   help="build the step's frames and launch sb_stylize_batch twice, no timing "
-                        "(a fixed launch sequence for ncu captures)")
+                   help="build the step's frames and launch sb_stylize_batch twice, then "
+                        "sb_lookup_only_batch twice, no timing (a fixed launch sequence for ncu "
+                        "captures)")
     return p.parse_args()
 
 
@@ -845,6 +846,9 @@ def profile_once(args):
              for i, f in enumerate(frames)]
     for _ in range(2):
         sb.stylize_batch(batch, w.blend_radius)
+    # then the lookup-only comparator over the same frames, batched, twice
+    for _ in range(2):
+        sb.lookup_only_batch(batch)
     torch.cuda.synchronize()
     print(json.dumps({"profile_once": w.name, "frames": len(batch)}))
 
