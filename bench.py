@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -112,15 +113,23 @@ def algorithmic_bytes(w, frame) -> dict:
     return dict(pixels=px, frame_bytes=guide_b + out_b, exemplar_bytes=ex_b)
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and with whitespace runs collapsed."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash() -> str:
-    """Hash of the sources the profiled batch kernel is compiled from (the
-    frame kernels' header, the shared device helpers and the per-format
-    translation units), so committed counters go stale when it changes."""
+    """Hash of the code the profiled batch kernel is compiled from (the frame
+    kernels' header, the shared device helpers and the per-format translation
+    units; comments and layout excluded), so committed counters go stale when
+    the code changes."""
     d = os.path.join(ROOT, "paper_1807_03249_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(d)):
         if f in ("sb_frame.cuh", "sb_internal.cuh") or (f.startswith("sb_frame_c") and f.endswith(".cu")):
-            h.update(open(os.path.join(d, f), "rb").read())
+            h.update(_code_only(open(os.path.join(d, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -958,7 +958,7 @@ __global__ void __launch_bounds__(kThreads) blend_kernel(const FrameArgs a) {
 }
 
 // Raises a kernel's dynamic shared-memory limit once per (kernel, device);
-// later launches of no larger size skip the driver call.  The cache is keyed
+// later launches of no larger size skip the runtime call.  The cache is keyed
 // by the kernel itself (one static per template instance).
 template <auto Kernel>
 cudaError_t ensure_smem(size_t smem) {
