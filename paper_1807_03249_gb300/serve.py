@@ -8,6 +8,8 @@ CUDA stream) is free and their device buffers fit the HBM budget.  Each
 admitted group runs as one sb_stylize_batch launch between its host-to-device
 and device-to-host copies on its slot's stream, so groups on different slots
 overlap on the device, and requests arriving meanwhile join the next group.
+Results return smallest first and a request is done as soon as its own result
+is back on the host.
 
 Each slot owns one device buffer (its arena) that holds its group's guides and
 outputs, so serving makes no device allocation per request: an arena grows in
@@ -112,7 +114,7 @@ class Server:
         # per slot: one device buffer that holds its group's guides and outputs
         self.arenas = [None] * slots
         self.exemplars = {}
-        self.inflight = []  # (event, slot, group)
+        self.inflight = []  # (slot, group, per-request events)
         self.max_loop_gap_s = 0.0
 
     _ALIGN = 256
@@ -190,26 +192,34 @@ class Server:
                 _, sd, lut = self.exemplars[r.exemplar]
                 frames.append(BatchFrame(g, lut, sd, r.levels, r.threshold, r.seed, out=o))
             stylize_batch(frames, self.radius, stream=s)
-            for r, f in zip(group, frames):
+            # results go back smallest first, each followed by its own event, so
+            # a small request is done as soon as its own copy is; the last event
+            # marks the group's (and the slot's) end
+            evs = [None] * len(group)
+            for i in sorted(range(len(group)), key=lambda i: group[i].pixels):
+                r, f = group[i], frames[i]
                 if r.out is None:
                     r.out = t.empty(f.out.shape, dtype=t.uint8, pin_memory=True)
                 r.out.copy_(f.out, non_blocking=True)
-            ev = t.cuda.Event()
-            ev.record(s)
+                evs[i] = t.cuda.Event()
+                evs[i].record(s)
         t_adm = now()
         for r in group:
             r.admitted = t_adm
-        self.inflight.append((ev, slot, group))
+            r.done = None
+        self.inflight.append((slot, group, evs))
 
     def poll(self, now: Callable[[], float]):
-        """Retires finished groups (frees their slot and bytes); returns their requests."""
+        """Stamps each request whose result is back on the host, retires
+        groups whose results all are (frees their slot and bytes) and returns
+        the requests of those groups."""
         done, still = [], []
         for item in self.inflight:
-            ev, slot, group = item
-            if ev.query():
-                t_done = now()
-                for r in group:
-                    r.done = t_done
+            slot, group, evs = item
+            for r, ev in zip(group, evs):
+                if r.done is None and ev.query():
+                    r.done = now()
+            if all(r.done is not None for r in group):
                 self.sched.finish(slot, group)
                 done.extend(group)
             else:
