@@ -98,6 +98,61 @@ def latency_summary(reqs, wall_s: float) -> dict:
             "wall_s": wall_s}
 
 
+class SlotArena:
+    """One slot's device buffer.  A group's guides and RGBA8 outputs are carved
+    from it as contiguous [H, W, C] views at 256-byte boundaries, and it grows
+    in 64 MiB steps to the largest group the slot has held.  The caller grows
+    or reuses it only while the slot is free (its previous group's work done)."""
+
+    ALIGN = 256
+    STEP = 64 << 20
+
+    def __init__(self, torch, device):
+        self.torch, self.device = torch, device
+        self.buf = None
+        self._typed = {}
+        self._off = 0
+
+    @classmethod
+    def aligned(cls, n: int) -> int:
+        return (n + cls.ALIGN - 1) // cls.ALIGN * cls.ALIGN
+
+    @classmethod
+    def request_bytes(cls, guide) -> int:
+        """Arena bytes of one request: its guide and RGBA8 output, each aligned."""
+        h, w = int(guide.shape[0]), int(guide.shape[1])
+        return cls.aligned(guide.element_size() * guide.numel()) + cls.aligned(4 * h * w)
+
+    @property
+    def capacity(self) -> int:
+        return 0 if self.buf is None else self.buf.numel()
+
+    def ensure(self, nbytes: int):
+        if self.capacity >= nbytes:
+            return
+        cap = max(1, -(-nbytes // self.STEP)) * self.STEP
+        self.buf, self._typed = None, {}
+        self.buf = self.torch.empty(cap, dtype=self.torch.uint8, device=self.device)
+
+    def start_group(self, nbytes: int):
+        """Makes room for a group of nbytes and carves from the start again."""
+        self.ensure(nbytes)
+        self._off = 0
+
+    def carve(self, dtype, shape):
+        """The next contiguous view of the given dtype and [H, W, C] shape."""
+        if dtype not in self._typed:
+            self._typed[dtype] = self.buf.view(dtype)
+        a = self._typed[dtype]
+        size = a.element_size()
+        nbytes = size * shape[0] * shape[1] * shape[2]
+        if self._off + nbytes > self.capacity:
+            raise ValueError(f"arena of {self.capacity} bytes cannot hold {self._off + nbytes}")
+        v = a.as_strided(tuple(shape), (shape[1] * shape[2], shape[2], 1), self._off // size)
+        self._off += self.aligned(nbytes)
+        return v
+
+
 class Server:
     """The loop bound to one CUDA device through the StyleBlit library."""
 
@@ -112,36 +167,16 @@ class Server:
         self.sched = Scheduler(budget_bytes, slots, min(max_batch, MAX_BATCH))
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
         # per slot: one device buffer that holds its group's guides and outputs
-        self.arenas = [None] * slots
+        self.arenas = [SlotArena(torch, self.device) for _ in range(slots)]
         self.exemplars = {}
         self.inflight = []  # (slot, group, per-request events)
         self.max_loop_gap_s = 0.0
-
-    _ALIGN = 256
-
-    @classmethod
-    def _aligned(cls, n: int) -> int:
-        return (n + cls._ALIGN - 1) // cls._ALIGN * cls._ALIGN
-
-    _ARENA_STEP = 64 << 20
-
-    def _ensure_arena(self, slot: int, nbytes: int):
-        # Grows in 64 MiB steps to the largest group the slot has held.  Only
-        # called while the slot is free: its previous group's work has completed.
-        buf = self.arenas[slot]
-        if buf is not None and buf.numel() >= nbytes:
-            return buf
-        cap = max(1, -(-nbytes // self._ARENA_STEP)) * self._ARENA_STEP
-        self.arenas[slot] = None
-        buf = self.torch.empty(cap, dtype=self.torch.uint8, device=self.device)
-        self.arenas[slot] = buf
-        return buf
 
     def reserve(self, nbytes_per_slot: int):
         """Sizes every slot's arena for groups of up to nbytes_per_slot bytes
         now, so that serving allocates no device memory afterwards."""
         for slot in self.sched.free_slots:
-            self._ensure_arena(slot, nbytes_per_slot)
+            self.arenas[slot].ensure(nbytes_per_slot)
 
     def add_exemplar(self, ex_id: int, guide, style, key_bits: int):
         """Uploads an exemplar and builds its table; both stay resident."""
@@ -155,8 +190,7 @@ class Server:
     def device_bytes(self, guide) -> int:
         """Device bytes of one request in its slot's arena: the guide and the
         RGBA8 output, each 256-byte aligned."""
-        h, w = int(guide.shape[0]), int(guide.shape[1])
-        return self._aligned(guide.element_size() * guide.numel()) + self._aligned(4 * h * w)
+        return SlotArena.request_bytes(guide)
 
     def submit(self, req: Request):
         req.nbytes = self.device_bytes(req.guide)
@@ -166,29 +200,16 @@ class Server:
         from . import BatchFrame, stylize_batch
         t = self.torch
         s = self.streams[slot]
-        arena = self._ensure_arena(slot, sum(r.nbytes for r in group))
-        typed = {}
-        off = 0
-
-        def carve(nbytes: int, dtype, shape):
-            # a contiguous [H, W, C] view at the next 256-byte boundary
-            nonlocal off
-            if dtype not in typed:
-                typed[dtype] = arena.view(dtype)
-            a = typed[dtype]
-            size = a.element_size()
-            v = a.as_strided(shape, (shape[1] * shape[2], shape[2], 1), off // size)
-            off += self._aligned(nbytes)
-            return v
-
+        arena = self.arenas[slot]
+        arena.start_group(sum(r.nbytes for r in group))
         with t.cuda.stream(s):
             frames = []
             for r in group:
-                h, w = int(r.guide.shape[0]), int(r.guide.shape[1])
-                g = carve(r.guide.element_size() * r.guide.numel(), r.guide.dtype,
-                          r.guide.shape)
-                g.copy_(r.guide, non_blocking=True)
-                o = carve(4 * h * w, t.uint8, (h, w, 4))
+                src = r.guide if r.guide.dim() == 3 else r.guide.unsqueeze(-1)
+                h, w = int(src.shape[0]), int(src.shape[1])
+                g = arena.carve(src.dtype, tuple(src.shape))
+                g.copy_(src, non_blocking=True)
+                o = arena.carve(t.uint8, (h, w, 4))
                 _, sd, lut = self.exemplars[r.exemplar]
                 frames.append(BatchFrame(g, lut, sd, r.levels, r.threshold, r.seed, out=o))
             stylize_batch(frames, self.radius, stream=s)
