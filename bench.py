@@ -53,6 +53,8 @@ def _args():
     p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-served", action="store_true")
+    p.add_argument("--no-4k", action="store_true",
+                   help="skip the 3840x2160 UV workload (batched and single-frame) on the line")
     p.add_argument("--no-uneven", action="store_true",
                    help="skip the uneven batch (64 mixed-size frames, 8 exemplars)")
     p.add_argument("--profile-once", action="store_true",
@@ -400,6 +402,10 @@ def run_gpu(args):
         barrier()
         return max_over_ranks(e0.elapsed_time(e1), world, dev)
 
+    def step_batch_persistent():
+        sb.stylize_batch(batch, w.blend_radius, stream=stream,
+                         schedule={"persistent": 1, "largest_first": 0})
+
     graph = capture(step_batch)
     graph_frames = capture(step_frames)
     for _ in range(max(3, args.warmup)):
@@ -426,6 +432,11 @@ def run_gpu(args):
     value = job_throughput(world, px_step, args.steps, ms)
     pf_steps = max(3, min(args.steps, 300))
     ms_pf = time_graph(graph_frames, pf_steps)
+    graph_persistent = capture(step_batch_persistent)
+    for _ in range(3):
+        with torch.cuda.stream(stream):
+            graph_persistent.replay()
+    ms_persistent = time_graph(graph_persistent, pf_steps)
 
     # the lookup-only comparator (Section 4, texture mapping) on the same frames:
     # one short launch per frame spread over four streams (forked from and
@@ -564,10 +575,17 @@ def run_gpu(args):
                                 "alone, same streams (the host link's ceiling for e2e)"}},
             "issue_roofline": issue,
             "per_frame_launch": per_frame,
+            "persistent_schedule": {
+                "value": job_throughput(world, px_step, pf_steps, ms_persistent),
+                "unit": "Mpixel/s", "ms_per_step": ms_persistent / pf_steps, "steps": pf_steps,
+                "launch": "CUDA graph of one sb_stylize_batch launch, persistent work-queue "
+                          "schedule (one CTA per resident slot, tiles taken from a queue)"},
             "lookup_only": lookup,
             "gpu_launches": args.steps,
             "lut_build_ms": min(t_lut),
             "clocks": clocks}
+    if rank == 0 and world == 1 and args.workload == "1080p" and not args.no_4k:
+        line["workload_4k"] = run_workload_4k(dev, min(args.steps, 300), max(3, args.warmup))
     if rank == 0 and world == 1 and not args.no_served:
         line["served"] = run_served(dev)
     if rank == 0 and world == 1 and not args.no_uneven:
@@ -678,6 +696,103 @@ def workload_stats(sb, g_tgt, g_src, lut, w, radius: int, n_sample: int = 20000,
                       "at frame borders)"}
 
 
+def run_workload_4k(dev, steps: int, warmup: int) -> dict:
+    """The 3840x2160 UV workload (L7, T 2^20, 7x7 vote, 2048^2 identity-UV
+    exemplar): one sb_stylize_batch launch over FRAMES_PER_STEP distinct
+    frames per step (a CUDA graph; inputs and outputs exceed L2), with its HBM
+    roofline and issue roofline, and the single-frame path (one sb_stylize
+    launch per frame, the same frames in turn, so no frame is L2-resident when
+    its launch starts)."""
+    import torch
+
+    import paper_1807_03249_gb300 as sb
+    w, frames = make_workload("4k", FRAMES_PER_STEP)
+    ex = w.exemplar
+    H, W = frames[0].shape[:2]
+    ab = algorithmic_bytes(w, frames[0])
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a.view(np.int16) if a.dtype == np.uint16
+                                                     else a)).to(dev)
+
+    gs, st = to_dev(ex.guide), to_dev(ex.style)
+    lut = sb.build_lut(gs, ex.lut_bits)
+    gts = [to_dev(f) for f in frames]
+    outs = [torch.empty((H, W, 4), dtype=torch.uint8, device=dev) for _ in frames]
+    batch = [sb.BatchFrame(gts[i], lut, st, w.levels, w.threshold, w.seed + i, out=outs[i])
+             for i in range(FRAMES_PER_STEP)]
+    stream = torch.cuda.Stream(dev)
+
+    def graph_of(fn):
+        with torch.cuda.stream(stream):
+            fn()
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            fn()
+        torch.cuda.synchronize()
+        for _ in range(warmup):
+            with torch.cuda.stream(stream):
+                g.replay()
+        torch.cuda.synchronize()
+        return g
+
+    def timed(g, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(n):
+                g.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    def singles():
+        for i in range(FRAMES_PER_STEP):
+            sb.stylize(gts[i], gs, st, lut, w.levels, w.threshold, w.blend_radius, w.seed + i,
+                       out=outs[i], stream=stream)
+
+    ms_batch = timed(graph_of(lambda: sb.stylize_batch(batch, w.blend_radius, stream=stream)),
+                     steps)
+    ms_single = timed(graph_of(singles), max(3, steps // 2)) / FRAMES_PER_STEP
+    lut.destroy()
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    alg = FRAMES_PER_STEP * ab["frame_bytes"] + ab["exemplar_bytes"]
+    achieved = alg / (ms_batch / 1e3) / 1e9
+    counters = profiled_counters("4k")
+    sm_mhz = peaks.get("sm_max_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue_peak = sms * 4 * sm_mhz * 1e6
+    inst = counters.get("warp_instructions_per_launch")
+    single_bytes = ab["frame_bytes"] + ab["exemplar_bytes"]
+    return {"workload": w.name, "frame": f"{W}x{H}", "frames_per_step": FRAMES_PER_STEP,
+            "levels": w.levels, "threshold": w.threshold,
+            "blend": f"{2 * w.blend_radius + 1}x{2 * w.blend_radius + 1}",
+            "value": job_throughput(1, FRAMES_PER_STEP * H * W, 1, ms_batch),
+            "unit": "Mpixel/s", "ms_per_step": ms_batch, "steps": steps,
+            "us_per_frame": 1e3 * ms_batch / FRAMES_PER_STEP,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm,
+                         "traffic": counters.get("dram_bytes_per_launch"),
+                         "kernel": f"batch_kernel<2,16,{w.blend_radius}> (sb_stylize_batch)",
+                         "algorithmic_bytes_per_launch": alg,
+                         "bytes_rule": "24 frames x (guide in + RGBA8 out) + exemplar "
+                                       "(style + guide + table) once per launch"},
+            "issue_roofline": {"bound": "issue", "unit": "warp instructions/s",
+                               "peak": issue_peak,
+                               "achieved": inst / (ms_batch / 1e3) if inst else None,
+                               "frac": inst / (ms_batch / 1e3) / issue_peak if inst else None,
+                               "instructions_per_launch": inst},
+            "single_frame": {"us_per_frame": 1e3 * ms_single,
+                             "value": H * W / (ms_single / 1e3) / 1e6, "unit": "Mpixel/s",
+                             "hbm_frac": single_bytes / (ms_single / 1e3) / 1e9 / hbm,
+                             "bytes_rule": "guide in + RGBA8 out + exemplar (style + guide + "
+                                           "table) per frame",
+                             "launch": "CUDA graph of 24 sb_stylize launches, one per frame"}}
+
+
 def run_uneven(dev, n_frames: int = 64, n_exemplars: int = 8, seed: int = 4000,
                steps: int = 20) -> dict:
     """The uneven batch: n_frames frames with widths uniform in [640, 3840]
@@ -736,6 +851,12 @@ def run_uneven(dev, n_frames: int = 64, n_exemplars: int = 8, seed: int = 4000,
     ms_batch = timed(lambda: sb.stylize_batch(frames, 2))
     best, _ = sb.autotune_batch(frames, 2, reps=3)
     ms_tuned = timed(lambda: sb.stylize_batch(frames, 2, schedule=best))
+    per_schedule = {}
+    for pers in (0, 1):
+        for lf in (0, 1):
+            sc = {"persistent": pers, "largest_first": lf}
+            per_schedule[f"persistent={pers},largest_first={lf}"] = timed(
+                lambda: sb.stylize_batch(frames, 2, schedule=sc))
     torch.cuda.synchronize()
     equal = all(torch.equal(f.out, o) for f, (_, _, _, _, _, o) in zip(frames, singles))
     for _, _, lut in exs:
@@ -747,6 +868,7 @@ def run_uneven(dev, n_frames: int = 64, n_exemplars: int = 8, seed: int = 4000,
             "autotuned_mpixel_per_s": px / (ms_tuned / 1e3) / 1e6,
             "autotuned_schedule": best, "equal_outputs": equal,
             "ms_per_step": {"per_frame": ms_pf, "batch": ms_batch, "autotuned": ms_tuned},
+            "ms_per_step_by_schedule": per_schedule,
             "workload": f"{n_frames} frames 640x360..3840x2160 (16:9), {n_exemplars} 1024^2 "
                         "sphere exemplars, L6 T300 5x5; each form a CUDA graph"}
 

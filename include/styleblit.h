@@ -133,9 +133,10 @@ SB_API sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, sb_lu
  *              the caller: receives the same entries sb_build_lut computes.
  *   stream     the build is enqueued on this stream.
  * Scratch: a fixed 1.1 MiB array inside the library (file-scope device memory,
- * held by every GPU that loads the library until the process exits).  The
- * first call on a device looks up that array's device address (once per
- * device, with the device current); make that first call before any stream
+ * held by every GPU that loads the library until the process exits).  Every
+ * call looks up that array's device address on the current device (no
+ * caching, so a device reset in between is harmless); the first call on a
+ * device may load the library's device code, so make it before any stream
  * capture.  All calls share the array and it keeps the last call's contents
  * (every call overwrites what it reads, nothing needs clearing): calls whose
  * GPU work overlaps (e.g. enqueued on different streams without ordering)

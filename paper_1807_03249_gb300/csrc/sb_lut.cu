@@ -16,9 +16,7 @@
 //      holds no pixel strictly closer than the best and no tie with a smaller
 //      linear index, so the result equals the brute-force argmin.
 #include <algorithm>
-#include <atomic>
 #include <cstdio>
-#include <mutex>
 
 #include "sb_internal.cuh"
 
@@ -500,26 +498,14 @@ constexpr int kStaticBoundsTiles = 65536;  // 1 MiB: 16x16 tiles of a 4096 x 409
 constexpr int kStaticSupers = 5376;        // their super-tiles, any aspect (sides <= 32767)
 static __device__ __align__(256) uint4 g_static_bounds[kStaticBoundsTiles + kStaticSupers];
 
-// Device address of g_static_bounds on the current device, looked up once per
-// device (host code cannot use the symbol itself as a device pointer).
+// Device address of g_static_bounds on the current device (host code cannot
+// use the symbol itself as a device pointer).  Looked up on every call, not
+// cached: after a device reset the module is loaded again and the array may
+// sit elsewhere.  cudaGetSymbolAddress allocates nothing.
 static cudaError_t static_bounds_address(uint4 **out) {
-    constexpr int kMaxDev = 64;
-    static std::atomic<uint4 *> addr[kMaxDev] = {};
-    static std::mutex mu;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    uint4 *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_static_bounds);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
-    uint4 *p = addr[dev].load(std::memory_order_acquire);
-    if (!p) {
-        std::lock_guard<std::mutex> lock(mu);
-        p = addr[dev].load(std::memory_order_relaxed);
-        if (!p) {
-            e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_static_bounds);
-            if (e != cudaSuccess) return e;
-            addr[dev].store(p, std::memory_order_release);
-        }
-    }
     *out = p;
     return cudaSuccess;
 }

@@ -1,6 +1,8 @@
 """sb_stylize_batch: many frames of mixed sizes, exemplars, levels, thresholds
 and seeds in one launch must give, frame by frame, exactly what sb_stylize
-gives for that frame alone (and, sampled, what the oracle gives)."""
+gives for that frame alone, and what the oracle gives."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -8,7 +10,7 @@ import torch
 import oracle
 import paper_1807_03249_gb300 as sb
 import synth
-from tests.gpu_helpers import sample_pixels, to_dev
+from tests.gpu_helpers import to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -52,20 +54,24 @@ def test_batch_equals_single_frame_calls(cuda_device, radius):
         assert np.array_equal(outs[k].cpu().numpy(), ref)
 
 
-def test_batch_full_size_frames_sampled(cuda_device):
+def test_batch_full_size_frames_persistent_whole_frames(cuda_device):
+    """Full-size 1080p frames through the persistent work-queue schedule,
+    largest frames first: every pixel equals the oracle."""
     w = synth.workload_1080p(2)
     ex = w.exemplar
     gs, st = to_dev(ex.guide, cuda_device), to_dev(ex.style, cuda_device)
     lut = sb.build_lut(gs, ex.lut_bits)
     frames = [sb.BatchFrame(to_dev(f.guide, cuda_device), lut, st, w.levels, w.threshold,
                             w.seed + i) for i, f in enumerate(w.frames)]
-    outs = sb.stylize_batch(frames, w.blend_radius)
+    outs = sb.stylize_batch(frames, w.blend_radius,
+                            schedule={"persistent": 1, "largest_first": 1})
     torch.cuda.synchronize()
+    ref_lut = oracle.new_lut(ex.guide.shape[2], ex.lut_bits)
     for i, f in enumerate(w.frames):
-        xs, ys = sample_pixels(40 + i, 1920, 1080, 40, w.blend_radius)
-        ref = oracle.stylize_points(f.guide, ex.guide, ex.style, ex.lut_bits, w.levels,
-                                    w.threshold, w.blend_radius, w.seed + i, xs, ys)
-        assert np.array_equal(outs[i].cpu().numpy()[ys, xs], ref)
+        ref, _, _ = oracle.stylize(f.guide, ex.guide, ex.style, ex.lut_bits, w.levels,
+                                   w.threshold, w.blend_radius, w.seed + i, lut=ref_lut,
+                                   n_threads=os.cpu_count() or 1)
+        assert np.array_equal(outs[i].cpu().numpy(), ref), f"frame {i}"
 
 
 def test_batch_argument_errors(cuda_device):

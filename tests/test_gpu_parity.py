@@ -2,10 +2,12 @@
 
 The bar is bit-exactness: look-up tables, assignment maps, level maps and
 RGBA8 outputs are integer results and must equal the oracle's element by
-element; the float vote must be within 1e-5 absolute.  Small cases compare
-whole frames; the 1920x1080 and 3840x2160 workloads compare sampled pixels
-(the oracle computes each one from scratch) and check full-frame properties.
+element; the float vote must be within 1e-5 absolute.  Every case compares
+whole frames, the 1920x1080 and 3840x2160 workloads included (several frames
+in one batched launch, as the benchmark runs them).
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -193,41 +195,44 @@ def test_blend_rgba8_and_f32_match_oracle(cuda_device, radius):
 
 
 # ---------------------------------------------------------------------------
-# full-size workloads: sampled pixels and full-frame properties
+# full-size workloads: whole frames against the oracle, in the launch
+# configuration the benchmark times (one sb_stylize_batch launch over several
+# frames), plus the single-frame and unfused paths and full-frame properties
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("name", ["1080p", "4k"])
-def test_full_size_sampled_parity_and_properties(cuda_device, name):
-    w = workload(name)
-    ex, fr = w.exemplar, w.frames[0]
-    H, W = fr.guide.shape[:2]
-    gt, gs, st = (to_dev(fr.guide, cuda_device), to_dev(ex.guide, cuda_device),
-                  to_dev(ex.style, cuda_device))
+@pytest.mark.parametrize("name,n_frames", [("1080p", 3), ("4k", 2)])
+def test_full_size_whole_frames_match_oracle(cuda_device, name, n_frames):
+    w = synth.workload_1080p(n_frames) if name == "1080p" else synth.workload_4k_uv(n_frames)
+    ex = w.exemplar
+    H, W = w.frames[0].guide.shape[:2]
+    gs, st = to_dev(ex.guide, cuda_device), to_dev(ex.style, cuda_device)
     lut = sb.build_lut(gs, ex.lut_bits)
-    out = sb.stylize(gt, gs, st, lut, w.levels, w.threshold, w.blend_radius, w.seed)
-    a, lev = sb.assign_chunks(gt, gs, lut, w.levels, w.threshold, w.seed)
-    out2 = sb.blend(a, st, w.blend_radius)
+    gts = [to_dev(f.guide, cuda_device) for f in w.frames]
+    seeds = [w.seed + 7919 * i for i in range(n_frames)]
+    batch = sb.stylize_batch([sb.BatchFrame(gts[i], lut, st, w.levels, w.threshold, seeds[i])
+                              for i in range(n_frames)], w.blend_radius)
+    single = sb.stylize(gts[0], gs, st, lut, w.levels, w.threshold, w.blend_radius, seeds[0])
+    maps = [sb.assign_chunks(g, gs, lut, w.levels, w.threshold, s) for g, s in zip(gts, seeds)]
+    unfused = sb.blend(maps[0][0], st, w.blend_radius)
     torch.cuda.synchronize()
-    out, A, lev, out2 = out.cpu().numpy(), u32(a), lev.cpu().numpy(), out2.cpu().numpy()
-    # fused == unfused on every pixel
-    assert np.array_equal(out, out2)
-    # sampled pixels against the oracle, each computed from scratch
-    xs, ys = sample_pixels(11, W, H, 120, w.blend_radius)
     ref_lut = oracle.new_lut(ex.guide.shape[2], ex.lut_bits)
-    ra, rl = oracle.assign_points(fr.guide, ex.guide, ex.lut_bits, w.levels, w.threshold, w.seed,
-                                  xs, ys, lut=ref_lut)
-    assert np.array_equal(A[ys, xs], ra)
-    assert np.array_equal(lev[ys, xs], rl)
-    k = 60
-    ro = oracle.stylize_points(fr.guide, ex.guide, ex.style, ex.lut_bits, w.levels, w.threshold,
-                               w.blend_radius, w.seed, xs[:k], ys[:k], lut=ref_lut)
-    assert np.array_equal(out[ys[:k], xs[:k]], ro)
-    # every accepted candidate above level 1 satisfies the threshold
-    Ax, Ay = (A & 0xFFFF).astype(np.int64), (A >> 16).astype(np.int64)
-    assert (Ax < ex.guide.shape[1]).all() and (Ay < ex.guide.shape[0]).all()
-    d = ((ex.guide[Ay, Ax].astype(np.int64) - fr.guide.astype(np.int64)) ** 2).sum(-1)
-    assert (d[lev > 1] <= w.threshold).all()
-    assert lev.min() >= 1 and lev.max() <= w.levels
+    for i, f in enumerate(w.frames):
+        ref_out, ref_a, ref_lev = oracle.stylize(f.guide, ex.guide, ex.style, ex.lut_bits,
+                                                 w.levels, w.threshold, w.blend_radius, seeds[i],
+                                                 lut=ref_lut, n_threads=os.cpu_count() or 1)
+        A, lev = u32(maps[i][0]), maps[i][1].cpu().numpy()
+        assert np.array_equal(A, ref_a), f"frame {i}: assignment"
+        assert np.array_equal(lev, ref_lev), f"frame {i}: levels"
+        assert np.array_equal(batch[i].cpu().numpy(), ref_out), f"frame {i}: batched RGBA8"
+        if i == 0:
+            assert np.array_equal(single.cpu().numpy(), ref_out), "single-frame RGBA8"
+            assert np.array_equal(unfused.cpu().numpy(), ref_out), "unfused RGBA8"
+            # every accepted candidate above level 1 satisfies the threshold
+            Ax, Ay = (A & 0xFFFF).astype(np.int64), (A >> 16).astype(np.int64)
+            assert (Ax < ex.guide.shape[1]).all() and (Ay < ex.guide.shape[0]).all()
+            d = ((ex.guide[Ay, Ax].astype(np.int64) - f.guide.astype(np.int64)) ** 2).sum(-1)
+            assert (d[lev > 1] <= w.threshold).all()
+            assert lev.min() >= 1 and lev.max() <= w.levels and (H, W) == A.shape
 
 
 # ---------------------------------------------------------------------------

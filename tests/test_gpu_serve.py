@@ -1,9 +1,11 @@
 """The serving loop: requests of mixed sizes and exemplars, admitted while
-others are on the GPU, give exactly the result each gives alone."""
+others are on the GPU, give exactly the result each gives alone, and that
+result equals the oracle's stylisation of the request."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_1807_03249_gb300 as sb
 import synth
 from paper_1807_03249_gb300.serve import Request, Server
@@ -32,11 +34,16 @@ def test_served_results_equal_each_request_alone(cuda_device):
     done, wall = srv.run(reqs, real_time=False)
     assert len(done) == len(reqs)
     assert srv.sched.peak_in_use <= srv.sched.budget and srv.sched.in_use == 0
+    ref_luts = {k: oracle.new_lut(3, 5) for k in exs}
     for r in reqs:
         gd, sd, lut = srv.exemplars[r.exemplar]
         alone = sb.stylize(r.guide.to(cuda_device), gd, sd, lut, r.levels, r.threshold, 2, r.seed)
         torch.cuda.synchronize()
         assert torch.equal(r.out, alone.cpu()), f"request {r.rid}"
+        g, stl = exs[r.exemplar]
+        ref, _, _ = oracle.stylize(r.guide.numpy(), g, stl, 5, r.levels, r.threshold, 2, r.seed,
+                                   lut=ref_luts[r.exemplar], n_threads=4)
+        assert np.array_equal(r.out.numpy(), ref), f"request {r.rid} vs oracle"
         assert r.done >= r.admitted >= r.arrival
 
 
@@ -63,7 +70,11 @@ def test_reserved_server_allocates_no_device_memory_while_serving(cuda_device):
     assert len(done) == len(reqs) and after == before
     _, sd, lut = srv.exemplars[0]
     gd = srv.exemplars[0][0]
+    ref_lut = oracle.new_lut(3, 5)
     for r in reqs:
         alone = sb.stylize(r.guide.to(cuda_device), gd, sd, lut, 5, 300, 2, r.seed)
         torch.cuda.synchronize()
         assert torch.equal(r.out, alone.cpu()), f"request {r.rid}"
+        ref, _, _ = oracle.stylize(r.guide.numpy(), g, st, 5, 5, 300, 2, r.seed, lut=ref_lut,
+                                   n_threads=4)
+        assert np.array_equal(r.out.numpy(), ref), f"request {r.rid} vs oracle"
