@@ -584,12 +584,12 @@ def run_gpu(args):
             "gpu_launches": args.steps,
             "lut_build_ms": min(t_lut),
             "clocks": clocks}
-    if rank == 0 and world == 1 and args.workload == "1080p" and not args.no_4k:
-        line["workload_4k"] = run_workload_4k(dev, min(args.steps, 300), max(3, args.warmup))
     if rank == 0 and world == 1 and not args.no_served:
         line["served"] = run_served(dev)
     if rank == 0 and world == 1 and not args.no_uneven:
         line["batched_uneven"] = run_uneven(dev)
+    if rank == 0 and world == 1 and args.workload == "1080p" and not args.no_4k:
+        line["workload_4k"] = run_workload_4k(dev, min(args.steps, 300), max(3, args.warmup))
     if rank == 0:
         line["workload_stats"] = workload_stats(sb, g_tgt[0], g_src, lut, w, w.blend_radius)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

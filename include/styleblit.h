@@ -182,7 +182,7 @@ SB_API sb_status sb_build_lut_keyed(const sb_guide *src_guide, int32_t key_bits,
  *   tgt_guide   target guide G_T (device).
  *   src_guide   source guide G_S (device), the one `lut` was built from.
  *   lut         table from sb_build_lut for src_guide.
- *   levels      L, 1 <= L <= 12; level l uses seed spacing 2^l.
+ *   levels      L, 1 <= L <= 15; level l uses seed spacing 2^l.
  *   threshold   t, compared as squared integer guide distance (<=).
  *   seed        frame seed of the jitter hash (re-randomise per frame for
  *               the controllable flicker of Section 3.3).
@@ -220,7 +220,7 @@ SB_API sb_status sb_blend(const uint32_t *assign, int32_t tgt_w, int32_t tgt_h,
  *
  *   tgt_guide, src_guide, lut, levels, threshold, seed: as sb_assign_chunks.
  *   src_style     C_S (device), same width and height as src_guide.
- *   blend_radius  r, 0 <= r <= 7.
+ *   blend_radius  r, 0 <= r <= 15.
  *   rgba8_out     device uint8[tgt h * tgt w * 4] (row-major, tightly packed).
  * Errors: SB_ERR_INVALID_ARG, SB_ERR_UNSUPPORTED, SB_ERR_CUDA.
  */
@@ -235,7 +235,7 @@ typedef struct {
     sb_guide tgt_guide;        /* target guide G_T of this frame */
     const sb_lut *lut;         /* table of this frame's exemplar (sb_build_lut) */
     sb_rgba8 src_style;        /* that exemplar's style C_S (same size as its guide) */
-    int32_t levels;            /* L, 1..12 */
+    int32_t levels;            /* L, 1..15 */
     uint64_t threshold;        /* t, squared guide distance, <= accepts */
     uint32_t seed;             /* frame seed of the jitter hash */
     uint8_t *rgba8_out;        /* tgt h * tgt w * 4 bytes, 4-byte aligned */
@@ -254,7 +254,7 @@ typedef struct {
  *                 the device data they point to must stay valid until the
  *                 stream reaches the batch).
  *   n_frames      0..128 (0 is a no-op).
- *   blend_radius  r, 0 <= r <= 7, for every frame.
+ *   blend_radius  r, 0 <= r <= 15, for every frame.
  * Allocates nothing.  Errors: SB_ERR_INVALID_ARG (a frame's arguments, as for
  * sb_stylize; the message names the frame), SB_ERR_UNSUPPORTED (frames with
  * different guide formats), SB_ERR_CUDA.
@@ -269,10 +269,20 @@ SB_API sb_status sb_stylize_batch(const sb_frame *frames, int32_t n_frames, int3
  *   persistent     0: one CTA per tile (the hardware issues tiles as CTAs
  *                  retire); 1: as many CTAs as fit on the device take tiles
  *                  from a work queue in device memory until the batch is done.
- *                  At most 64 persistent launches may be in flight at once
- *                  (each takes one of 64 queue slots in turn); the queue
- *                  resets itself at the end of a launch, so CUDA graph replays
- *                  are fine.
+ *                  The queue resets itself at the end of a launch.  Queues
+ *                  come from a fixed set of 1024 per device, assigned so that
+ *                  no two launches that may run at once share one: a stream
+ *                  keeps one queue for all its eager persistent launches
+ *                  (they run one after another), and a launch captured into a
+ *                  CUDA graph gets a queue of its own, never reused, which
+ *                  every replay of that executable graph uses (CUDA orders the
+ *                  replays of one executable graph).  Not supported: running
+ *                  two executable graphs instantiated from the same capture at
+ *                  the same time, and destroying a stream while its persistent
+ *                  launch runs and launching on a new stream that received
+ *                  the same handle.  Once 1024 streams and captured launches
+ *                  have taken queues on a device, further persistent launches
+ *                  there fail with SB_ERR_UNSUPPORTED.
  *   largest_first  0: tiles in frame order; 1: frames with more tiles first
  *                  (shorter tail for uneven batches).
  */

@@ -6,15 +6,16 @@
 // assignment A of the tile plus a halo of R pixels (the vote window) in shared
 // memory, so A never reaches device memory:
 //
-//   phase 0  target guide of the region -> smem (one packed uint32 per pixel),
-//            read by vertical segments of 4 pixels (one region column per
-//            lane); the seed cells of every level >= 3 are built at the same
-//            time (levels 2 and 1 have many cells and are built only if a
-//            pixel of the tile still needs them).  A cell is: jitter hash ->
-//            seed q clamped into the target -> G_T[q] -> table entry u*(q).
-//            Cells are stored column-major (x outer, y inner), each as
-//            (-2q, |q|^2, u*) in region-centred coordinates, pre-scaled by
-//            2^11 with the cell's column-major index in the low 11 bits.
+//   phase 0  target guide of the region -> smem (one packed uint32 per pixel,
+//            row-major, thread t loads pixels t, t + 256, ...); the seed cells
+//            of every level >= 3 are built at the same time (levels 2 and 1
+//            have many cells and are built only if a pixel of the tile still
+//            needs them).  A cell is: jitter hash -> seed q clamped into the
+//            target -> G_T[q] -> table entry u*(q).  Cells are stored
+//            column-major (x outer, y inner), each as (-2q, |q|^2) in
+//            region-centred coordinates pre-scaled by 2^11 with the cell's
+//            column-major index in the low 11 bits, plus the translation
+//            u* - q packed.
 //   levels   for l = L..1 while pixels are pending: a pixel p takes the
 //            minimum over its 3 x 3 cells of |q|^2 - 2 q.p (which orders seeds
 //            like |q - p|^2) packed with the cell index: one min gives the
@@ -22,18 +23,22 @@
 //            order, as NearestSeed's strict < does.  The candidate
 //            s = u* + (p - q) is accepted if it lies in the source and
 //            |G_S[s] - G_T[p]|^2 <= t (level 1 always accepts, s clamped).
-//            Work goes by the 4-pixel segments: a segment lies in one cell at
-//            levels >= 2 and the pixels choosing a seed form a convex set, so
-//            when its first and last pending pixels choose the same seed all
-//            of them do and the search runs once.  Segments with rejected
-//            pixels are compacted into the next level's list.
-//   vote     ballot bitmasks mark, per row, where A steps by exactly one pixel
-//            (horizontally and vertically); a window made of one translation
-//            votes exactly C_S[A(p)], a plain copy.  Other pixels (chunk
-//            boundaries, frame borders) are compacted and summed over the full
-//            window with integer sums and round-half-up division.
+//            Work goes by vertical segments of 4 pixels, one region column per
+//            lane: a segment lies in one cell at levels >= 2 and the keys are
+//            affine in p, so its four keys per cell are one multiply-add and
+//            three adds.  Segments with rejected pixels are compacted into the
+//            next level's list.
+//   vote     ballots mark, per region row, where A steps by exactly one pixel
+//            (E, horizontally) and where it continues the row above (V); one
+//            thread per row turns them into 64-bit masks of the output columns
+//            whose window row is one run or at most two runs, one thread per
+//            output row ANDs them over the window.  A window made of one
+//            translation votes exactly C_S[A(p)], a plain copy; a window whose
+//            rows have at most two runs sums one gather per run; the rest
+//            (junctions, frame borders) sum tap by tap.  Integer sums,
+//            round-half-up division.
 //   store    uniform windows store from the copy pass (coalesced rows), the
-//            others from the full-window passes.
+//            others from the two list passes.
 #pragma once
 
 #include <atomic>
@@ -50,6 +55,10 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kEagerMinLevel = 3;           // levels >= this get their cells in phase 0
 constexpr int kKeyShift = 11;               // cell-index bits of the packed seed key
 constexpr int kPackedMaxLevel = 8;          // levels whose packed keys fit 32 bits
+// Packed-level cells hold u* - q (q region-centred) with this bias on both
+// axes, packed x | y << 16: seeds of those levels lie within 600 pixels of the
+// region centre, so both fields stay within 16 bits.
+constexpr int kShiftBias = 1024;
 
 enum Mode { kAssign = 0, kStylize = 1 };
 
@@ -85,7 +94,10 @@ struct SmemLayout {
     size_t off_cells, off_gt, off_A, off_list0, off_list1, off_bytes, off_masks, off_cnt, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int r, int levels) {
+// Shared memory of one tile.  The vote's masks overlay the target guide of
+// the region, which is dead once the assignment is done; the level bytes exist
+// only for the assignment-only kernel (the fused path never stores levels).
+__host__ __device__ inline SmemLayout smem_layout(int r, int levels, bool level_bytes = false) {
     SmemLayout s;
     s.RW = kTW + 2 * r;
     s.RH = kTH + 2 * r;
@@ -96,23 +108,29 @@ __host__ __device__ inline SmemLayout smem_layout(int r, int levels) {
     s.off_cells = o;
     o += sizeof(int4) * (size_t)s.NC;
     s.off_gt = o;
+    // vote masks: per region row E, V (4 words each), hu, t2, vc (64-bit);
+    // per output row U, T2 (64-bit); they fit in the guide's 4 NR bytes
+    s.off_masks = o;
     o += sizeof(uint32_t) * (size_t)s.NR;
     s.off_A = o;
     o += sizeof(uint32_t) * (size_t)s.NR;
-    s.off_masks = o;
-    o += (2 * sizeof(uint64_t) + 4 * sizeof(uint32_t)) * (size_t)s.RH;
     s.off_list0 = o;
     o += sizeof(uint16_t) * (size_t)s.NR;
     s.off_list1 = o;
     o += sizeof(uint16_t) * (size_t)s.NR;
     s.off_bytes = o;
-    o += (size_t)s.NR;
+    if (level_bytes) o += (size_t)s.NR;
     o = (o + 15) & ~(size_t)15;
     s.off_cnt = o;
-    o += 32;  // 3 level counters (rotating), slow and complex vote counters
+    o += 32;  // 3 level counters (rotating), the vote's two list lengths
     s.total = o;
     return s;
 }
+__host__ __device__ constexpr bool vote_masks_fit(int r) {
+    return (8 * 4 + 3 * 8) * (kTH + 2 * r) + 2 * 8 * kTH <= 4 * (kTW + 2 * r) * (kTH + 2 * r) &&
+           (r == 15 || vote_masks_fit(r + 1));
+}
+static_assert(vote_masks_fit(0), "the vote masks fit in the region guide's shared memory");
 
 // Block-wide append to a shared list; every lane of the warp must call it.
 __device__ __forceinline__ void list_push(bool pred, int val, uint16_t *list, int *counter) {
@@ -157,17 +175,11 @@ struct CellTask {
     int l, ci, sx, sy;
 };
 
-__device__ __forceinline__ CellTask cell_task(const FrameArgs &a, int k, int l_hi, int xa, int xb,
-                                              int ya, int yb) {
+// Cell ci (column-major) of level l, whose cells are g.
+__device__ __forceinline__ CellTask cell_at(const FrameArgs &a, int l, int ci,
+                                            const LevelCells &g) {
     CellTask t;
-    int l = l_hi, off = 0;
-    LevelCells g = level_cells(l, xa, xb, ya, yb);
-    while (k >= off + g.ncx * g.ncy) {
-        off += g.ncx * g.ncy;
-        --l;
-        g = level_cells(l, xa, xb, ya, yb);
-    }
-    const int ci = k - off;  // column-major: ci = lcx * ncy + lcy
+    // column-major: ci = lcx * ncy + lcy
     // ci / ncy through a float reciprocal: ci < 2^11 and ncy < 2^6 keep the
     // true quotient at least 0.5 / ncy from an integer, far above the
     // rounding error, so the truncation is exact
@@ -185,15 +197,42 @@ __device__ __forceinline__ CellTask cell_task(const FrameArgs &a, int k, int l_h
     return t;
 }
 
-// The stored cell: (-2q, |q|^2, u*) in region-centred coordinates (q - (cxo,
-// cyo)); levels with packed keys scale by 2^11 and add the cell index.
+__device__ __forceinline__ CellTask cell_task(const FrameArgs &a, int k, int l_hi, int xa, int xb,
+                                              int ya, int yb) {
+    int l = l_hi, off = 0;
+    LevelCells g = level_cells(l, xa, xb, ya, yb);
+    while (k >= off + g.ncx * g.ncy) {
+        off += g.ncx * g.ncy;
+        --l;
+        g = level_cells(l, xa, xb, ya, yb);
+    }
+    return cell_at(a, l, k - off, g);
+}
+
+// The stored cell, in region-centred coordinates (q - (cxo, cyo)): levels
+// with packed keys hold (-2q, |q|^2) scaled by 2^11 with the cell index added
+// to |q|^2 (computed modulo 2^32: only the keys built from it, which fit 32
+// bits, are used) and the translation u* - q biased by kShiftBias, packed, so
+// a pixel's candidate u* + (p - q) is one add; coarser levels hold (-q, 0, u*)
+// and their keys are squared distances in 64 bits.
 __device__ __forceinline__ int4 cell_value(const CellTask &t, uint32_t u, int cxo, int cyo) {
     const int qx = t.sx - cxo, qy = t.sy - cyo;
     if (t.l <= kPackedMaxLevel) {
-        constexpr int S = 1 << kKeyShift;
-        return make_int4(-2 * qx * S, -2 * qy * S, (qx * qx + qy * qy) * S + t.ci, (int)u);
+        constexpr uint32_t S = 1u << kKeyShift;
+        const uint32_t z = ((uint32_t)(qx * qx) + (uint32_t)(qy * qy)) * S + (uint32_t)t.ci;
+        const uint32_t d = (uint32_t)((int)(u & 0xFFFFu) - qx + kShiftBias) |
+                           ((uint32_t)((int)(u >> 16) - qy + kShiftBias) << 16);
+        return make_int4((int)((uint32_t)(-2 * qx) * S), (int)((uint32_t)(-2 * qy) * S), (int)z,
+                         (int)d);
     }
-    return make_int4(-2 * qx, -2 * qy, qx * qx + qy * qy, (int)u);
+    return make_int4(-qx, -qy, 0, (int)u);
+}
+
+// Packed region-centred position (px, py) minus the bias: added to a cell's
+// packed translation it gives the packed candidate.  A coordinate below zero
+// borrows and lands far above any source side (in_source fails).
+__device__ __forceinline__ uint32_t biased_pos(int px, int py) {
+    return (uint32_t)((px - kShiftBias) + (py - kShiftBias) * 65536);
 }
 
 // Builds cells k0, k0 + kThreads, ... of the levels l_hi down to l_lo into
@@ -254,25 +293,27 @@ struct SrcView {
     const uint32_t *src_packed;
     int Ws, Hs;
     uint64_t threshold;
+    // packed position v = x | y << 16 inside the source
+    __device__ __forceinline__ bool in_source(uint32_t v) const {
+        return (v & 0xFFFFu) < (uint32_t)Ws && v < ((uint32_t)Hs << 16);
+    }
 };
 
 // Candidate test of the pixels of one segment: pixel j sits at region index
-// ibase + j * RW and its candidate source position is (sx[j], sy[j]).
+// ibase + j * RW and its candidate source position is the packed v[j].
 // Accepted pixels get A (and the level); the bits of rejected pixels of m
 // are returned.
 template <int C, int B, int RW>
 __device__ __forceinline__ uint32_t test_segment(const SrcView &a, const uint32_t *gt,
                                                  uint32_t *A, uint8_t *lev, int l, uint32_t t32,
-                                                 uint32_t m, int ibase, const int (&sx)[4],
-                                                 const int (&sy)[4]) {
+                                                 uint32_t m, int ibase, const uint32_t (&v)[4]) {
     using F = GuideFmt<C, B>;
     uint32_t gsv[4];
     bool ok[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        ok[j] = ((m >> j) & 1u) && (unsigned)sx[j] < (unsigned)a.Ws &&
-                (unsigned)sy[j] < (unsigned)a.Hs;
-        gsv[j] = ok[j] ? __ldg(a.src_packed + ((uint32_t)sy[j] * (uint32_t)a.Ws + (uint32_t)sx[j]))
+        ok[j] = ((m >> j) & 1u) && a.in_source(v[j]);
+        gsv[j] = ok[j] ? __ldg(a.src_packed + ((v[j] >> 16) * (uint32_t)a.Ws + (v[j] & 0xFFFFu)))
                        : 0u;
     }
     uint32_t rej = 0;
@@ -286,7 +327,7 @@ __device__ __forceinline__ uint32_t test_segment(const SrcView &a, const uint32_
             else acc = d <= a.threshold;
         }
         if (acc) {
-            A[ibase + j * RW] = (uint32_t)sx[j] + ((uint32_t)sy[j] << 16);
+            A[ibase + j * RW] = v[j];
             if (lev) lev[ibase + j * RW] = (uint8_t)l;
         }
         rej |= (uint32_t)!acc << j;
@@ -295,9 +336,9 @@ __device__ __forceinline__ uint32_t test_segment(const SrcView &a, const uint32_
 }
 
 // Levels where every pixel searches its own seed: level 1 (a segment spans
-// two cells) and the levels above kPackedMaxLevel (unscaled cells, 64-bit
-// keys).  Both are rare, so pixels go one at a time with little live state
-// (the common path keeps its registers).
+// two cells) and the levels above kPackedMaxLevel (keys are 64-bit squared
+// distances packed with the cell index).  Both are rare, so pixels go one at
+// a time with little live state (the common path keeps its registers).
 template <int C, int B, int R>
 __device__ __forceinline__ uint32_t segment_level_rare(const SrcView &a, const uint32_t *gt,
                                                        uint32_t *A, uint8_t *lev,
@@ -320,14 +361,20 @@ __device__ __forceinline__ uint32_t segment_level_rare(const SrcView &a, const u
         for (int d = 0; d < 9; ++d) {
             const int c = cj + (d / 3 - 1) * ncy + (d % 3 - 1);
             const int4 cl = cells[c];
-            const int e = cl.z + cl.x * prx + cl.y * (pry + j);
-            // packed cells carry the index in their low bits already
-            key = min(key, packed ? (long long)e : (((long long)e << kKeyShift) | (c - base)));
+            if (packed) {
+                // packed cells carry the index in their low bits already
+                key = min(key, (long long)(int)((uint32_t)cl.z + (uint32_t)cl.x * (uint32_t)prx +
+                                                (uint32_t)cl.y * (uint32_t)(pry + j)));
+            } else {
+                const long long dx = prx + cl.x, dy = pry + j + cl.y;
+                key = min(key, ((dx * dx + dy * dy) << kKeyShift) | (c - base));
+            }
         }
         const int4 cl = cells[base + (int)(key & kMask)];
-        const int sh = packed ? kKeyShift + 1 : 1;
-        int sx = (int)((uint32_t)cl.w & 0xFFFFu) + prx + (cl.x >> sh);
-        int sy = (int)((uint32_t)cl.w >> 16) + pry + j + (cl.y >> sh);
+        // packed cells: translation u* - q (biased); the others: u* and -q
+        const int ox = packed ? -kShiftBias : cl.x, oy = packed ? -kShiftBias : cl.y;
+        int sx = (int)((uint32_t)cl.w & 0xFFFFu) + prx + ox;
+        int sy = (int)((uint32_t)cl.w >> 16) + pry + j + oy;
         const int i = (ry + j) * RW + rx;
         bool acc = true;
         if (l == 1) {
@@ -370,51 +417,35 @@ __device__ __forceinline__ uint32_t segment_level(const FrameArgs &a, const uint
     const int prx = rx - RW / 2, pry = ry - RH / 2;
     const int c0 = base + (((rx0 + rx) >> l) - g.cx0) * g.ncy + (((ry0 + ry) >> l) - g.cy0);
     const int ibase = ry * RW + rx;
-    int sx[4], sy[4];
-    auto candidate = [&](int j, int key) {
-        const int4 cl = cells[base + (key & kMask)];
-        sx[j] = (int)((uint32_t)cl.w & 0xFFFFu) + prx + (cl.x >> (kKeyShift + 1));
-        sy[j] = (int)((uint32_t)cl.w >> 16) + pry + j + (cl.y >> (kKeyShift + 1));
-    };
     const SrcView sv{a.src_packed, a.Ws, a.Hs, a.threshold};
     if (l == 1 || l > kPackedMaxLevel)
         return segment_level_rare<C, B, R>(sv, gt, A, lev, cells, base, c0, g.ncy, l, t32, rx, ry,
                                            m);
-    const int jlo = __ffs(m) - 1, jhi = 31 - __clz(m);
-    int klo = INT_MAX, khi = INT_MAX;
-#pragma unroll
+    // every lane evaluates the nine keys at all four pixels (three adds per
+    // cell on top of the first pixel's key): no lane waits for a neighbour
+    // whose segment straddles a Voronoi edge
+    int k[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+#pragma unroll 1
     for (int dx = -1; dx <= 1; ++dx) {
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
             const int4 cl = cells[c0 + dx * g.ncy + dy];
-            const int e = cl.z + cl.x * prx + cl.y * (pry + jlo);
-            klo = min(klo, e);
-            khi = min(khi, e + (jhi - jlo) * cl.y);
-        }
-    }
-    if (((klo ^ khi) & kMask) == 0) {
-        candidate(0, klo);
+            // modulo 2^32: the keys themselves fit 32 bits
+            uint32_t e = (uint32_t)cl.z + (uint32_t)cl.x * (uint32_t)prx +
+                         (uint32_t)cl.y * (uint32_t)pry;
 #pragma unroll
-        for (int j = 1; j < 4; ++j) {
-            sx[j] = sx[0];
-            sy[j] = sy[0] + j;
-        }
-    } else {
-        int k[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-#pragma unroll
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int4 cl = cells[c0 + dx * g.ncy + dy];
-                const int e = cl.z + cl.x * prx + cl.y * pry;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) k[j] = min(k[j], e + j * cl.y);
+            for (int j = 0; j < 4; ++j) {
+                k[j] = min(k[j], (int)e);
+                e += (uint32_t)cl.y;
             }
         }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) candidate(j, k[j]);
     }
-    return test_segment<C, B, RW>(sv, gt, A, lev, l, t32, m, ibase, sx, sy);
+    // candidate of pixel j: its seed cell's packed translation plus p
+    const uint32_t P = biased_pos(prx, pry);
+    uint32_t v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = (uint32_t)cells[base + (k[j] & kMask)].w + P + (j << 16);
+    return test_segment<C, B, RW>(sv, gt, A, lev, l, t32, m, ibase, v);
 }
 
 // One level over segments: the top level (top) visits every segment of the region
@@ -480,42 +511,60 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
         cnt[0] = 0;
         cnt[1] = 0;
     }
-    // phase 0: every global load (the guide at this thread's first seed, the
+    // phase 0: every global load (the guide at this thread's seed, the
     // region's guide, then the seed's table entry) is issued before the
-    // first store that waits on one
-    const int n_eager = cell_count(L_top, eager_lo, xa, xb, ya, yb);
+    // first store that waits on one.  Thread k builds eager cell k (levels
+    // L_top .. eager_lo stacked, each column-major); the level of its cell is
+    // found while counting them.
+    int n_eager = 0, my_l = 0, my_ci = 0;
+    LevelCells my_g{};
+    for (int l = L_top; l >= eager_lo; --l) {
+        const LevelCells g = level_cells(l, xa, xb, ya, yb);
+        const int n = g.ncx * g.ncy;
+        if (tid >= n_eager && tid < n_eager + n) {
+            my_l = l;
+            my_ci = tid - n_eager;
+            my_g = g;
+        }
+        n_eager += n;
+    }
     const bool has_cell = tid < n_eager;
     CellTask ct{};
     uint32_t cg = 0;
     if (has_cell) {
-        ct = cell_task(a, tid, L_top, xa, xb, ya, yb);
+        ct = cell_at(a, my_l, my_ci, my_g);
         cg = F::load(a.tgt, a.tgt_stride, ct.sx, ct.sy);
     }
-    constexpr int kSegIters = (Segs<R>::NS + kThreads - 1) / kThreads;
-    uint32_t gv[kSegIters][4], itq[kSegIters];
+    // the region's guide, row-major: thread t takes pixels t, t + 256, ...
+    constexpr int NR = RW * RH;
+    constexpr int kIt = (NR + kThreads - 1) / kThreads;
+    constexpr int kStepY = kThreads / RW, kStepX = kThreads % RW;
+    uint32_t gv[kIt];
+    uint32_t inside = 0;  // bit k: pixel tid + k * 256 lies in the target
+    {
+        int rx = tid % RW, ry = tid / RW;
 #pragma unroll
-    for (int q = 0; q < kSegIters; ++q) {
-        const int sg = q * kThreads + tid;
-        const int rx = Segs<R>::rx(sg), ry = Segs<R>::ry(sg);
-        const uint32_t it = sg < Segs<R>::NS ? tb.template mask<R>(rx, ry) : 0u;
-        itq[q] = it;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            gv[q][j] = ((it >> j) & 1u) ? F::load(a.tgt, a.tgt_stride, rx0 + rx, ry0 + ry + j) : 0u;
+        for (int k = 0; k < kIt; ++k) {
+            const int gx = rx0 + rx, gy = ry0 + ry;
+            const bool in = (k + 1 < kIt || tid + k * kThreads < NR) && (unsigned)gx < (unsigned)a.W &&
+                            (unsigned)gy < (unsigned)a.H;
+            gv[k] = in ? F::load(a.tgt, a.tgt_stride, gx, gy) : 0u;
+            inside |= (uint32_t)in << k;
+            rx += kStepX;
+            ry += kStepY;
+            if (rx >= RW) {
+                rx -= RW;
+                ++ry;
+            }
+        }
     }
     uint32_t cu = 0;
     if (has_cell) cu = __ldg(a.lut + F::key(cg, a.key_bits, a.key_channels));
 #pragma unroll
-    for (int q = 0; q < kSegIters; ++q) {
-        const int sg = q * kThreads + tid;
-        if (sg >= Segs<R>::NS) continue;
-        const int rx = Segs<R>::rx(sg), ry = Segs<R>::ry(sg);
-        const uint32_t rl = Segs<R>::rows(ry);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (!((rl >> j) & 1u)) continue;
-            const int i = (ry + j) * RW + rx;
-            if ((itq[q] >> j) & 1u) gt[i] = gv[q][j];
+    for (int k = 0; k < kIt; ++k) {
+        const int i = tid + k * kThreads;
+        if (k + 1 < kIt || i < NR) {
+            if ((inside >> k) & 1u) gt[i] = gv[k];
             else A[i] = kInvalid;
         }
     }
@@ -635,198 +684,269 @@ __device__ __forceinline__ void vote_store(const FrameArgs &a, const Acc &acc, i
     }
 }
 
-// Full-window vote of the listed pixels.  Along a window row, taps whose A
-// steps by exactly one pixel form a run sharing one source position
-// v = A(n) - o, so a run contributes len * C_S[v] with a single gather.  A
-// row's run breaks come from the stored step bits E.  Pass 1 sums every
-// listed pixel as if each window row had at most two runs (branch-free: two
-// gathers per row) and compacts the pixels where some row has more breaks
-// (junctions of chunks, frame borders) into a second list; pass 2 sums those
-// tap by tap.  Every lane of a warp runs pass 1's loop the same number of
-// times.  Pass 1 reads the calling warp's own list (no block barrier before
-// it); pass 2 takes the block's complex pixels together (they are few).
+// Source position of window tap o = (ox, oy) of a neighbour whose assignment
+// is An: v = A(p + o) - o, packed x | y << 16.  A coordinate that drops below
+// zero borrows and lands far above any source side, so in_source() rejects
+// it; so does every tap of a neighbour outside the target (kInvalid).
+__device__ __forceinline__ uint32_t tap_pos(uint32_t An, int ox, int oy) {
+    return An - (uint32_t)(ox + oy * 65536);
+}
+
+struct StyleView {
+    const uint32_t *style32;
+    uint32_t stride, Ws, Hs16;  // row stride in pixels, source width, source height << 16
+    __device__ __forceinline__ static StyleView of(const FrameArgs &a) {
+        return StyleView{reinterpret_cast<const uint32_t *>(a.style), (uint32_t)a.style_stride_px,
+                         (uint32_t)a.Ws, (uint32_t)a.Hs << 16};
+    }
+    __device__ __forceinline__ bool in_source(uint32_t v) const {
+        return (v & 0xFFFFu) < Ws && v < Hs16;
+    }
+    __device__ __forceinline__ uint32_t at(uint32_t v) const {
+        return __ldg(style32 + ((v >> 16) * stride + (v & 0xFFFFu)));
+    }
+    // cnt taps whose source position is v (nothing when cnt == 0 or v is
+    // outside the source)
+    template <typename Acc>
+    __device__ __forceinline__ void add(Acc &acc, uint32_t v, uint32_t cnt) const {
+        const bool ok = cnt != 0u && in_source(v);
+        acc.add(ok ? at(v) : 0u, ok ? cnt : 0u);
+    }
+};
+
+// Step bits of window row ry for output column tx: bit i (0 <= i < 2R) is set
+// when taps i and i + 1 of that row belong to one run (A steps by exactly one
+// pixel between them).  E holds four words per region row (the fourth zero).
+template <int R>
+__device__ __forceinline__ uint32_t window_steps(const uint32_t *E, int ry, int tx) {
+    constexpr uint32_t kM = (1u << (2 * R)) - 1u;
+    const uint32_t *e = E + ry * 4;
+    const int b = tx + 1;
+    return __funnelshift_r(e[b >> 5], e[(b >> 5) + 1], b & 31) & kM;
+}
+
+// Windows whose rows have at most two runs each: one gather per run (the
+// second has length 0 in a single-run row).
 template <int R, bool F32>
-__device__ __forceinline__ void vote_slow_list(const FrameArgs &a, const uint32_t *A,
-                                               const uint32_t *E, const uint16_t *slow,
-                                               int n_slow, uint16_t *cplx, int *cplx_cnt,
-                                               int x0, int y0) {
+__device__ __forceinline__ void vote_two_runs(const FrameArgs &a, const StyleView &sv,
+                                              const uint32_t *A, const uint32_t *E,
+                                              const uint16_t *list, int n, int x0, int y0) {
     constexpr int RW = kTW + 2 * R;
     constexpr bool kPacked = (2 * R + 1) * (2 * R + 1) * 255 < 65536;
-    constexpr uint32_t kBreakMask = (2 * R >= 32) ? 0xFFFFFFFFu : ((1u << (2 * R)) - 1u);
-    const uint32_t *style32 = reinterpret_cast<const uint32_t *>(a.style);
-    const int sstride = a.style_stride_px;
-    auto tap = [&](VoteAcc<kPacked> &acc, const uint32_t *row, int tx, int col, int oy,
-                   uint32_t len) {
-        const uint32_t c = row[col];
-        const uint32_t v = c - (uint32_t)((col - tx - R) + (oy << 16));
-        const uint32_t vx = v & 0xFFFFu, vy = v >> 16;
-        // an out-of-target tap (kInvalid) lands out of the source here
-        const bool ok = len != 0u && vx < (uint32_t)a.Ws && vy < (uint32_t)a.Hs;
-        const uint32_t colr = ok ? __ldg(style32 + (vy * (uint32_t)sstride + vx)) : 0u;
-        acc.add(colr, ok ? len : 0u);
-    };
-    const int lane = threadIdx.x & 31;
-    for (int j0 = 0; j0 < n_slow; j0 += 32) {
-        const int j = j0 + lane;
-        const bool act = j < n_slow;
-        const int k = act ? slow[j] : 0;
-        const int tx = k % kTW, ty = k / kTW;
-        bool complex_row = false;
-        if (act) {
-            VoteAcc<kPacked> acc;
-#pragma unroll
-            for (int oy = -R; oy <= R; ++oy) {
-                const int ry = ty + R + oy;
-                const uint32_t *row = A + ry * RW;
-                const uint32_t *e = E + ry * 4;
-                const int b = tx + 1, w = b >> 5;
-                const uint32_t m = ~__funnelshift_r(e[w], e[w + 1], b & 31) & kBreakMask;
-                const int pc = __popc(m);
-                complex_row |= pc > 1;
-                const int j1 = pc ? __ffs(m) - 1 : 2 * R;
-                tap(acc, row, tx, tx, oy, (uint32_t)(j1 + 1));
-                tap(acc, row, tx, min(tx + j1 + 1, tx + 2 * R), oy,
-                    pc == 1 ? (uint32_t)(2 * R - j1) : 0u);
-            }
-            if (!complex_row) vote_store<F32, R>(a, acc, x0 + tx, y0 + ty);
-        }
-        list_push(act && complex_row, k, cplx, cplx_cnt);
-    }
-    __syncthreads();
-    const int n_cplx = *cplx_cnt;
-    for (int j = threadIdx.x; j < n_cplx; j += kThreads) {
-        const int k = cplx[j];
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+        const int k = list[j];
         const int tx = k % kTW, ty = k / kTW;
         VoteAcc<kPacked> acc;
-        for (int oy = -R; oy <= R; ++oy) {
-            const uint32_t *row = A + (ty + R + oy) * RW;
 #pragma unroll
-            for (int ox = 0; ox <= 2 * R; ++ox) tap(acc, row, tx, tx + ox, oy, 1u);
+        for (int oy = -R; oy <= R; ++oy) {
+            const int ry = ty + R + oy;
+            const uint32_t *row = A + ry * RW;
+            const int j1 = __ffs(~window_steps<R>(E, ry, tx));  // first run: taps [0, j1)
+            sv.add(acc, tap_pos(row[tx], -R, oy), (uint32_t)j1);
+            const int c2 = min(tx + j1, tx + 2 * R);
+            sv.add(acc, tap_pos(row[c2], c2 - tx - R, oy), (uint32_t)(2 * R + 1 - j1));
         }
         vote_store<F32, R>(a, acc, x0 + tx, y0 + ty);
     }
 }
 
-// bits [j, j + 64) of the 128-bit value hi:lo
+// Every other window (junctions of three or more chunks, frame borders): tap
+// by tap.  The block's such pixels share one list.
+template <int R, bool F32>
+__device__ __forceinline__ void vote_taps(const FrameArgs &a, const StyleView &sv,
+                                          const uint32_t *A, const uint16_t *list, int n, int x0,
+                                          int y0) {
+    constexpr int RW = kTW + 2 * R;
+    constexpr bool kPacked = (2 * R + 1) * (2 * R + 1) * 255 < 65536;
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+        const int k = list[j];
+        const int tx = k % kTW, ty = k / kTW;
+        VoteAcc<kPacked> acc;
+        for (int oy = -R; oy <= R; ++oy) {
+            const uint32_t *row = A + (ty + R + oy) * RW + tx + R;
+#pragma unroll
+            for (int ox = -R; ox <= R; ++ox) sv.add(acc, tap_pos(row[ox], ox, oy), 1u);
+        }
+        vote_store<F32, R>(a, acc, x0 + tx, y0 + ty);
+    }
+}
+
+// bits [j, j + 64) of the 128-bit value hi:lo, 0 <= j < 64
 __device__ __forceinline__ uint64_t shr128(uint64_t lo, uint64_t hi, int j) {
     return j == 0 ? lo : ((lo >> j) | (hi << (64 - j)));
 }
+
+// Shared-memory words of the vote's masks: per region row E (4 words), V (4
+// words) and the 64-bit output-column masks hu, t2, vc; per output row the
+// 64-bit class masks U and T2.
+template <int R>
+struct VoteMasks {
+    static constexpr int RH = kTH + 2 * R;
+    uint32_t *E, *V;
+    uint64_t *hu, *t2, *vc, *U, *T2;
+    __device__ __forceinline__ static VoteMasks at(unsigned char *p) {
+        VoteMasks m;
+        m.E = reinterpret_cast<uint32_t *>(p);
+        m.V = m.E + 4 * RH;
+        m.hu = reinterpret_cast<uint64_t *>(m.V + 4 * RH);
+        m.t2 = m.hu + RH;
+        m.vc = m.t2 + RH;
+        m.U = m.vc + RH;
+        m.T2 = m.U + kTH;
+        return m;
+    }
+};
 
 template <int R, bool F32>
 __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &L, int x0,
                                           int y0, const uint32_t *A, unsigned char *smem) {
     constexpr int RW = kTW + 2 * R, RH = kTH + 2 * R;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint64_t *hu_row = reinterpret_cast<uint64_t *>(smem + L.off_masks);
-    uint64_t *v_row = hu_row + RH;
-    uint32_t *E_row = reinterpret_cast<uint32_t *>(v_row + RH);  // 4 words per region row
-    // each warp lists the pixels of its own output rows: 8 slots x 32 lanes
-    constexpr int kWarpList = kTH / kWarps * 2 * 32;
-    uint16_t *slow = reinterpret_cast<uint16_t *>(smem + L.off_list0) + warp * kWarpList;
-    uint16_t *cplx = reinterpret_cast<uint16_t *>(smem + L.off_list1);
-    int *cplx_cnt = reinterpret_cast<int *>(smem + L.off_cnt) + 3;
-    const uint32_t *style32 = reinterpret_cast<const uint32_t *>(a.style);
-    const int sstride = a.style_stride_px;
+    const StyleView sv = StyleView::of(a);
+    const VoteMasks<R> mk = VoteMasks<R>::at(smem + L.off_masks);
+    if (R > 0 && threadIdx.x == 0) {
+        int *cnt = reinterpret_cast<int *>(smem + L.off_cnt);
+        cnt[3] = cnt[4] = 0;  // two-runs and tap-by-tap list lengths
+    }
 
-    if (threadIdx.x == 0) *cplx_cnt = 0;
     if constexpr (R > 0) {
-        // per region row: E bit x <=> A[x] == A[x-1] + 1 (both valid);
-        // hu bit tx <=> E bits tx+1 .. tx+2R all set (columns tx..tx+2R form
-        // one horizontal translation); v bit tx <=> A[ry][tx+R] == A[ry-1][tx+R]
-        // one row down (both valid)
+        // per region row: E bit x <=> A[x] == A[x-1] + 1, V bit x <=>
+        // A[ry][x] == A[ry-1][x] + (0, 1) (never true next to kInvalid)
         for (int ry = warp; ry < RH; ry += kWarps) {
             const uint32_t *row = A + ry * RW;
-            uint32_t e[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const int x = c * 32 + lane;
-                bool bit = false;
-                if (x >= 1 && x < RW) {
-                    const uint32_t cur = row[x], prv = row[x - 1];
-                    bit = cur == prv + 1u;  // never true next to kInvalid
+                bool eb = false, vb = false;
+                if (x < RW) {
+                    const uint32_t cur = row[x];
+                    eb = x >= 1 && cur == row[x - 1] + 1u;
+                    vb = ry >= 1 && cur == row[x - RW] + 0x10000u;
                 }
-                e[c] = __ballot_sync(0xFFFFFFFFu, bit);
-            }
-            const uint64_t lo = (uint64_t)e[0] | ((uint64_t)e[1] << 32), hi = e[2];
-            uint64_t hu = ~0ull;
-#pragma unroll
-            for (int j = 1; j <= 2 * R; ++j) hu &= shr128(lo, hi, j);
-            uint32_t v[2];
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int x = c * 32 + lane + R;
-                bool bit = false;
-                if (ry >= 1) {
-                    const uint32_t cur = row[x], up = row[x - RW];
-                    bit = cur == up + 0x10000u;
+                const uint32_t e = __ballot_sync(0xFFFFFFFFu, eb);
+                const uint32_t v = __ballot_sync(0xFFFFFFFFu, vb);
+                if (lane == 0) {
+                    mk.E[4 * ry + c] = e;
+                    mk.V[4 * ry + c] = v;
                 }
-                v[c] = __ballot_sync(0xFFFFFFFFu, bit);
             }
-            if (lane == 0) {
-                hu_row[ry] = hu;
-                v_row[ry] = (uint64_t)v[0] | ((uint64_t)v[1] << 32);
-                E_row[4 * ry + 0] = e[0];
-                E_row[4 * ry + 1] = e[1];
-                E_row[4 * ry + 2] = e[2];
-                E_row[4 * ry + 3] = 0u;
-            }
+            if (lane == 0) mk.E[4 * ry + 3] = mk.V[4 * ry + 3] = 0u;
         }
+        __syncthreads();
+        // one thread per region row, 64 output columns at once: hu bit tx <=>
+        // window row tx..tx+2R is one run; t2 <=> at most two runs; vc <=> the
+        // centre column is linked to the row above
+        if (threadIdx.x < RH) {
+            const int ry = threadIdx.x;
+            const uint32_t *e = mk.E + 4 * ry, *v = mk.V + 4 * ry;
+            const uint64_t blo = ~((uint64_t)e[0] | ((uint64_t)e[1] << 32)), bhi = ~(uint64_t)e[2];
+            uint64_t seen = 0, two = 0;
+#pragma unroll
+            for (int s = 1; s <= 2 * R; ++s) {
+                const uint64_t b = shr128(blo, bhi, s);
+                two |= seen & b;
+                seen |= b;
+            }
+            mk.hu[ry] = ~seen;
+            mk.t2[ry] = ~two;
+            mk.vc[ry] = shr128((uint64_t)v[0] | ((uint64_t)v[1] << 32), v[2], R);
+        }
+        __syncthreads();
+        // one thread per output row: uniform windows (one translation) and
+        // windows whose rows have at most two runs
+        if (threadIdx.x < kTH) {
+            const int ty = threadIdx.x;
+            uint64_t U = mk.hu[ty], T2 = mk.t2[ty];
+#pragma unroll
+            for (int k = 1; k <= 2 * R; ++k) {
+                U &= mk.hu[ty + k] & mk.vc[ty + k];
+                T2 &= mk.t2[ty + k];
+            }
+            mk.U[ty] = U;
+            mk.T2[ty] = T2 & ~U;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     // output rows: warp w takes rows w, w + 8, ...; a uniform window copies
     constexpr int kRowsPerWarp = kTH / kWarps;
     uint32_t col[kRowsPerWarp][2];
-    bool uni[kRowsPerWarp][2], need[kRowsPerWarp][2];
+    bool uni[kRowsPerWarp][2];
 #pragma unroll
     for (int q = 0; q < kRowsPerWarp; ++q) {
         const int ty = warp + q * kWarps;
         uint64_t U = ~0ull;
-        if constexpr (R > 0) {
-            // lane j < 2R + 1 brings window row ty + j; one AND-reduction per half
-            uint64_t m = ~0ull;
-            if (lane <= 2 * R) m = hu_row[ty + lane] & (lane > 0 ? v_row[ty + lane] : ~0ull);
-            U = (uint64_t)__reduce_and_sync(0xFFFFFFFFu, (uint32_t)m) |
-                ((uint64_t)__reduce_and_sync(0xFFFFFFFFu, (uint32_t)(m >> 32)) << 32);
-        }
+        if constexpr (R > 0) U = mk.U[ty];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int tx = c * 32 + lane;
-            const int gx = x0 + tx, gy = y0 + ty;
-            uni[q][c] = need[q][c] = false;
+            uni[q][c] = false;
             col[q][c] = 0;
-            if (gx < a.W && gy < a.H) {
-                const uint32_t cc = A[(ty + R) * RW + tx + R];
-                const int cx = (int)(cc & 0xFFFFu), cy = (int)(cc >> 16);
-                const bool ok = ((U >> tx) & 1ull) && cx < a.Ws && cy < a.Hs;
-                uni[q][c] = ok;
-                need[q][c] = !ok;
-                if (ok) col[q][c] = __ldg(style32 + ((uint32_t)cy * (uint32_t)sstride + (uint32_t)cx));
+            if (x0 + tx < a.W && y0 + ty < a.H && ((U >> tx) & 1ull)) {
+                const uint32_t v = A[(ty + R) * RW + tx + R];
+                uni[q][c] = sv.in_source(v);
+                if (uni[q][c]) col[q][c] = sv.at(v);
             }
         }
     }
-    const unsigned lt = (1u << lane) - 1u;
-    int n_slow = 0;
+    // stores of the copies; the other pixels go to two block-wide lists (a
+    // warp counts its entries with ballots, then reserves its ranges with one
+    // atomic per list)
+    unsigned mg[kRowsPerWarp][2], mt[kRowsPerWarp][2];
+    int n_g = 0, n_t = 0;
 #pragma unroll
     for (int q = 0; q < kRowsPerWarp; ++q) {
         const int ty = warp + q * kWarps;
+        uint64_t T2 = 0;
+        if constexpr (R > 0) T2 = mk.T2[ty];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int tx = c * 32 + lane;
-            const int k = ty * kTW + tx;
-            if (uni[q][c]) {
+            const bool in = x0 + tx < a.W && y0 + ty < a.H;
+            // R = 0: the only tap is p itself; outside the source it votes 0
+            if (uni[q][c] || (R == 0 && in)) {
                 if constexpr (F32) {
-                    a.f32_out[(int64_t)(y0 + ty) * a.W + x0 + tx] = rgba_f32(col[q][c]);
+                    a.f32_out[(int64_t)(y0 + ty) * a.W + x0 + tx] = uni[q][c] ? rgba_f32(col[q][c]) : make_float4(0.f, 0.f, 0.f, 0.f);
                 } else {
                     a.rgba_out[(int64_t)(y0 + ty) * a.W + x0 + tx] = col[q][c];
                 }
             }
-            const unsigned nm = __ballot_sync(0xFFFFFFFFu, need[q][c]);
-            if (need[q][c]) slow[n_slow + __popc(nm & lt)] = (uint16_t)k;
-            n_slow += __popc(nm);
+            if constexpr (R > 0) {
+                const bool g = in && ((T2 >> tx) & 1ull);
+                mg[q][c] = __ballot_sync(0xFFFFFFFFu, g);
+                mt[q][c] = __ballot_sync(0xFFFFFFFFu, in && !uni[q][c] && !g);
+                n_g += __popc(mg[q][c]);
+                n_t += __popc(mt[q][c]);
+            }
         }
     }
-    __syncwarp();
-    vote_slow_list<R, F32>(a, A, E_row, slow, n_slow, cplx, cplx_cnt, x0, y0);
+    if constexpr (R > 0) {
+        int *cnt = reinterpret_cast<int *>(smem + L.off_cnt);
+        uint16_t *glist = reinterpret_cast<uint16_t *>(smem + L.off_list0);
+        uint16_t *tlist = reinterpret_cast<uint16_t *>(smem + L.off_list1);
+        int bg = 0, bt = 0;
+        if (lane == 0) {
+            if (n_g) bg = atomicAdd(&cnt[3], n_g);
+            if (n_t) bt = atomicAdd(&cnt[4], n_t);
+        }
+        bg = __shfl_sync(0xFFFFFFFFu, bg, 0);
+        bt = __shfl_sync(0xFFFFFFFFu, bt, 0);
+        const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+        for (int q = 0; q < kRowsPerWarp; ++q) {
+            const int ty = warp + q * kWarps;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int k = ty * kTW + c * 32 + lane;
+                if ((mg[q][c] >> lane) & 1u) glist[bg + __popc(mg[q][c] & lt)] = (uint16_t)k;
+                if ((mt[q][c] >> lane) & 1u) tlist[bt + __popc(mt[q][c] & lt)] = (uint16_t)k;
+                bg += __popc(mg[q][c]);
+                bt += __popc(mt[q][c]);
+            }
+        }
+        __syncthreads();
+        vote_two_runs<R, F32>(a, sv, A, mk.E, glist, cnt[3], x0, y0);
+        vote_taps<R, F32>(a, sv, A, tlist, cnt[4], x0, y0);
+    }
 }
 
 // One 64 x 32 output tile (tile_x, tile_y) of one frame.
@@ -857,8 +977,9 @@ __device__ __forceinline__ void frame_tile(const FrameArgs &a, const SmemLayout 
 
 // CTAs per SM the kernels are compiled for: four (64 registers a thread) hide
 // more of each tile's load latency than three with 80 registers; five (48)
-// spill too much.
-__host__ __device__ constexpr int min_ctas(int) { return 4; }
+// spill too much.  Windows above 15 x 15 need more than a quarter of the
+// SM's shared memory anyway, so they are compiled for one CTA per SM.
+__host__ __device__ constexpr int min_ctas(int r) { return r <= 7 ? 4 : 1; }
 
 template <int C, int B, int MODE, int R>
 __global__ void __launch_bounds__(kThreads, min_ctas(R))
@@ -903,26 +1024,24 @@ __global__ void __launch_bounds__(kThreads, min_ctas(R))
     batch_tile<C, B, R>(b, L, (int)blockIdx.x, smem);
 }
 
-// Work queues of persistent batch launches: CTAs take the next tile from
+// Work queue of a persistent batch launch: CTAs take the next tile from
 // `next` until the batch is exhausted; the last CTA to leave clears the queue
-// for the next launch (CUDA graph replays included).  A launch uses slot
-// `slot`; launches in flight at the same time need distinct slots.  No CTA
-// waits on another.
+// for the next launch that uses it (CUDA graph replays included).  The host
+// hands every launch a queue no launch that may run at the same time holds
+// (sb_frame_api.cu).  No CTA waits on another.
 struct TileQueue {
     unsigned int next, done;
 };
-constexpr int kQueueSlots = 64;
-static __device__ TileQueue g_tile_queues[kQueueSlots];
 
 template <int C, int B, int R>
 __global__ void __launch_bounds__(kThreads, min_ctas(R))
-    batch_kernel_persistent(const __grid_constant__ BatchArgs b, const SmemLayout L, int slot) {
+    batch_kernel_persistent(const __grid_constant__ BatchArgs b, const SmemLayout L,
+                            TileQueue *q) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int tile;
-    TileQueue &q = g_tile_queues[slot];
     const int n_tiles = b.tile_start[b.n];
     for (;;) {
-        if (threadIdx.x == 0) tile = (int)atomicAdd(&q.next, 1u);
+        if (threadIdx.x == 0) tile = (int)atomicAdd(&q->next, 1u);
         __syncthreads();
         const int t = tile;
         __syncthreads();  // every thread has read `tile` before it is overwritten
@@ -932,9 +1051,9 @@ __global__ void __launch_bounds__(kThreads, min_ctas(R))
     }
     if (threadIdx.x == 0) {
         // this CTA takes no more tiles; the last one out resets the queue
-        if (atomicAdd(&q.done, 1u) == gridDim.x - 1) {
-            atomicExch(&q.next, 0u);
-            atomicExch(&q.done, 0u);
+        if (atomicAdd(&q->done, 1u) == gridDim.x - 1) {
+            atomicExch(&q->next, 0u);
+            atomicExch(&q->done, 0u);
         }
     }
 }
@@ -1016,11 +1135,11 @@ int persistent_grid(size_t smem, int n_tiles) {
 }
 
 template <int C, int B, int R>
-cudaError_t launch_batch_r(const BatchArgs &b, int max_levels, bool persistent, cudaStream_t s) {
+cudaError_t launch_batch_r(const BatchArgs &b, int max_levels, TileQueue *queue, cudaStream_t s) {
     // one layout (for the deepest frame) serves every tile of the launch
     const SmemLayout L = smem_layout(R, max_levels);
     const int n_tiles = b.tile_start[b.n];
-    if (!persistent) {
+    if (!queue) {
         cudaError_t e = ensure_smem<batch_kernel<C, B, R>>(L.total);
         if (e != cudaSuccess) return e;
         batch_kernel<C, B, R><<<n_tiles, kThreads, L.total, s>>>(b, L);
@@ -1028,27 +1147,25 @@ cudaError_t launch_batch_r(const BatchArgs &b, int max_levels, bool persistent, 
     }
     cudaError_t e = ensure_smem<batch_kernel_persistent<C, B, R>>(L.total);
     if (e != cudaSuccess) return e;
-    static std::atomic<unsigned> next_slot{0};
-    const int slot = (int)(next_slot.fetch_add(1u) % kQueueSlots);
     const int grid = persistent_grid<batch_kernel_persistent<C, B, R>>(L.total, n_tiles);
-    batch_kernel_persistent<C, B, R><<<grid, kThreads, L.total, s>>>(b, L, slot);
+    batch_kernel_persistent<C, B, R><<<grid, kThreads, L.total, s>>>(b, L, queue);
     return cudaGetLastError();
 }
 
-// Launches the batch kernel of guide format <C, B> for blend radius r.
-template <int C, int B>
-cudaError_t launch_batch(const BatchArgs &b, int r, int max_levels, bool persistent,
+// Launches the batch kernel of guide format <C, B> for blend radius r: one CTA
+// per tile (queue == nullptr) or persistent CTAs over the given work queue.
+template <int C, int B, int R = 0>
+cudaError_t launch_batch(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
                          cudaStream_t s) {
-    switch (r) {
-        case 0: return launch_batch_r<C, B, 0>(b, max_levels, persistent, s);
-        case 1: return launch_batch_r<C, B, 1>(b, max_levels, persistent, s);
-        case 2: return launch_batch_r<C, B, 2>(b, max_levels, persistent, s);
-        case 3: return launch_batch_r<C, B, 3>(b, max_levels, persistent, s);
-        case 4: return launch_batch_r<C, B, 4>(b, max_levels, persistent, s);
-        case 5: return launch_batch_r<C, B, 5>(b, max_levels, persistent, s);
-        case 6: return launch_batch_r<C, B, 6>(b, max_levels, persistent, s);
-        case 7: return launch_batch_r<C, B, 7>(b, max_levels, persistent, s);
-    }
+    if (r == R) return launch_batch_r<C, B, R>(b, max_levels, queue, s);
+    if constexpr (R < kMaxFusedRadius) return launch_batch<C, B, R + 1>(b, r, max_levels, queue, s);
+    return cudaErrorInvalidValue;
+}
+
+template <int C, int B, int R = 0>
+cudaError_t launch_stylize(const FrameArgs &a, cudaStream_t s) {
+    if (a.radius == R) return launch_stylize_r<C, B, R>(a, s);
+    if constexpr (R < kMaxFusedRadius) return launch_stylize<C, B, R + 1>(a, s);
     return cudaErrorInvalidValue;
 }
 
@@ -1056,35 +1173,25 @@ cudaError_t launch_batch(const BatchArgs &b, int r, int max_levels, bool persist
 template <int C, int B>
 cudaError_t launch_frame(int mode, const FrameArgs &a, cudaStream_t s) {
     if (mode == kAssign) {
-        const SmemLayout L = smem_layout(0, a.levels);
+        const SmemLayout L = smem_layout(0, a.levels, true);
         return launch_tiles<frame_kernel<C, B, kAssign, 0>>(L.total, a.W, a.H, s, a, L);
     }
-    switch (a.radius) {
-        case 0: return launch_stylize_r<C, B, 0>(a, s);
-        case 1: return launch_stylize_r<C, B, 1>(a, s);
-        case 2: return launch_stylize_r<C, B, 2>(a, s);
-        case 3: return launch_stylize_r<C, B, 3>(a, s);
-        case 4: return launch_stylize_r<C, B, 4>(a, s);
-        case 5: return launch_stylize_r<C, B, 5>(a, s);
-        case 6: return launch_stylize_r<C, B, 6>(a, s);
-        case 7: return launch_stylize_r<C, B, 7>(a, s);
-    }
-    return cudaErrorInvalidValue;
+    return launch_stylize<C, B>(a, s);
 }
 
 // per-format launchers, one translation unit each (sb_frame_c<C>b<B>.cu)
 // per-format batch launchers, defined next to the frame launchers
-cudaError_t launch_batch_c1b8(const BatchArgs &b, int r, int max_levels, bool persistent,
+cudaError_t launch_batch_c1b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
                               cudaStream_t s);
-cudaError_t launch_batch_c2b8(const BatchArgs &b, int r, int max_levels, bool persistent,
+cudaError_t launch_batch_c2b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
                               cudaStream_t s);
-cudaError_t launch_batch_c3b8(const BatchArgs &b, int r, int max_levels, bool persistent,
+cudaError_t launch_batch_c3b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
                               cudaStream_t s);
-cudaError_t launch_batch_c4b8(const BatchArgs &b, int r, int max_levels, bool persistent,
+cudaError_t launch_batch_c4b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
                               cudaStream_t s);
-cudaError_t launch_batch_c1b16(const BatchArgs &b, int r, int max_levels, bool persistent,
+cudaError_t launch_batch_c1b16(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
                               cudaStream_t s);
-cudaError_t launch_batch_c2b16(const BatchArgs &b, int r, int max_levels, bool persistent,
+cudaError_t launch_batch_c2b16(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
                               cudaStream_t s);
 cudaError_t launch_frame_c1b8(int mode, const FrameArgs &a, cudaStream_t s);
 cudaError_t launch_frame_c2b8(int mode, const FrameArgs &a, cudaStream_t s);

@@ -4,7 +4,9 @@
 #include <algorithm>
 #include <climits>
 #include <cstdio>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 
 #include "sb_frame.cuh"
 
@@ -29,21 +31,87 @@ static cudaError_t launch_frame_any(int channels, int bits, int mode, const Fram
 }
 
 static cudaError_t launch_batch_any(int channels, int bits, const BatchArgs &b, int r,
-                                    bool persistent, int max_levels, cudaStream_t s) {
+                                    TileQueue *queue, int max_levels, cudaStream_t s) {
     if (bits == 8) {
         switch (channels) {
-            case 1: return launch_batch_c1b8(b, r, max_levels, persistent, s);
-            case 2: return launch_batch_c2b8(b, r, max_levels, persistent, s);
-            case 3: return launch_batch_c3b8(b, r, max_levels, persistent, s);
-            case 4: return launch_batch_c4b8(b, r, max_levels, persistent, s);
+            case 1: return launch_batch_c1b8(b, r, max_levels, queue, s);
+            case 2: return launch_batch_c2b8(b, r, max_levels, queue, s);
+            case 3: return launch_batch_c3b8(b, r, max_levels, queue, s);
+            case 4: return launch_batch_c4b8(b, r, max_levels, queue, s);
         }
     } else if (bits == 16) {
         switch (channels) {
-            case 1: return launch_batch_c1b16(b, r, max_levels, persistent, s);
-            case 2: return launch_batch_c2b16(b, r, max_levels, persistent, s);
+            case 1: return launch_batch_c1b16(b, r, max_levels, queue, s);
+            case 2: return launch_batch_c2b16(b, r, max_levels, queue, s);
         }
     }
     return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Work queues of persistent batch launches.  Two launches must never share a
+// queue while both may run.  Launches on one stream run one after the other,
+// so an eager launch uses the queue its stream owns (assigned on the stream's
+// first persistent launch and kept).  A launch captured into a CUDA graph may
+// be replayed at any time on any stream, so it gets a queue of its own that no
+// other launch ever receives; replays of one executable graph are ordered by
+// CUDA, so they never overlap each other.  All formats and radii draw from one
+// array per device.
+// ---------------------------------------------------------------------------
+constexpr int kQueueSlots = 1024;
+__device__ TileQueue g_tile_queues[kQueueSlots];
+
+struct QueuePool {
+    std::mutex mu;
+    int used = 0;                                    // slots handed out so far
+    std::unordered_map<uintptr_t, int> by_stream;    // eager launches: stream -> slot
+    TileQueue *base = nullptr;                       // device address of g_tile_queues
+};
+
+static sb_status acquire_queue(cudaStream_t s, TileQueue **out) {
+    constexpr int kMaxDev = 64;
+    static QueuePool pools[kMaxDev];
+    static thread_local int per_thread_slot[kMaxDev] = {};  // slot + 1 for cudaStreamPerThread
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "sb_stylize_batch: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDev) return fail(SB_ERR_UNSUPPORTED, "device ordinal above 63");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess)
+        return cuda_fail(e, "sb_stylize_batch: cudaStreamIsCapturing");
+    QueuePool &P = pools[dev];
+    std::lock_guard<std::mutex> lock(P.mu);
+    // the array's address is looked up outside captures (a device reset may
+    // move it) and reused inside them
+    if (cap == cudaStreamCaptureStatusNone || !P.base) {
+        void *p = nullptr;
+        if ((e = cudaGetSymbolAddress(&p, g_tile_queues)) != cudaSuccess)
+            return cuda_fail(e, "sb_stylize_batch: work-queue address");
+        P.base = static_cast<TileQueue *>(p);
+    }
+    int slot = -1;
+    if (cap != cudaStreamCaptureStatusNone) {
+        if (P.used < kQueueSlots) slot = P.used++;
+    } else if (s == cudaStreamPerThread) {
+        // one handle, a different stream on every thread
+        if (!per_thread_slot[dev] && P.used < kQueueSlots) per_thread_slot[dev] = ++P.used;
+        slot = per_thread_slot[dev] - 1;
+    } else {
+        const uintptr_t key = reinterpret_cast<uintptr_t>(s == cudaStreamLegacy ? nullptr : s);
+        auto it = P.by_stream.find(key);
+        if (it != P.by_stream.end()) {
+            slot = it->second;
+        } else if (P.used < kQueueSlots) {
+            slot = P.used++;
+            P.by_stream.emplace(key, slot);
+        }
+    }
+    if (slot < 0)
+        return fail(SB_ERR_UNSUPPORTED,
+                    "sb_stylize_batch: no free work queue for a persistent launch (1024 per "
+                    "device: one per stream plus one per captured launch)");
+    *out = P.base + slot;
+    return SB_OK;
 }
 
 template <bool F32, int R>
@@ -87,7 +155,7 @@ static sb_status check_frame(const sb_guide *tgt, const sb_guide *src, const sb_
         lut->src_h != src->height)
         return fail(SB_ERR_INVALID_ARG, "lut was built for a different source guide format/size");
     if (levels < 1 || levels > kMaxLevels)
-        return fail(SB_ERR_INVALID_ARG, "levels must be in [1, 12]");
+        return fail(SB_ERR_INVALID_ARG, "levels must be in [1, 15]");
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != lut->device) return fail(SB_ERR_INVALID_ARG, "lut lives on another device");
@@ -147,7 +215,7 @@ extern "C" sb_status sb_stylize(const sb_guide *tgt_guide, const sb_guide *src_g
     if (src_style->width != src_guide->width || src_style->height != src_guide->height)
         return fail(SB_ERR_INVALID_ARG, "src_style and src_guide differ in size");
     if (blend_radius < 0 || blend_radius > kMaxFusedRadius)
-        return fail(SB_ERR_INVALID_ARG, "blend_radius must be in [0, 7]");
+        return fail(SB_ERR_INVALID_ARG, "blend_radius must be in [0, 15]");
     if ((int64_t)tgt_guide->width * tgt_guide->height == 0) return ok();
     if (!rgba8_out || ((uintptr_t)rgba8_out % 4))
         return fail(SB_ERR_INVALID_ARG, "rgba8_out: NULL or not 4-byte aligned");
@@ -210,7 +278,7 @@ static sb_status prepare_batch(const sb_frame *frames, int32_t n_frames, int32_t
     if (n_frames == 0) return ok();
     if (!frames) return fail(SB_ERR_INVALID_ARG, "frames: NULL");
     if (blend_radius < 0 || blend_radius > kMaxFusedRadius)
-        return fail(SB_ERR_INVALID_ARG, "blend_radius must be in [0, 7]");
+        return fail(SB_ERR_INVALID_ARG, "blend_radius must be in [0, 15]");
     b.n = n_frames;
     b.tile_start[0] = 0;
     max_levels = 1;
@@ -236,7 +304,7 @@ static sb_status prepare_batch(const sb_frame *frames, int32_t n_frames, int32_t
             return fail(SB_ERR_INVALID_ARG, std::string(name) + ": size differs from the lut's guide");
         std::snprintf(name, sizeof name, "frames[%d]", k);
         if (f.levels < 1 || f.levels > kMaxLevels)
-            return fail(SB_ERR_INVALID_ARG, std::string(name) + ": levels must be in [1, 12]");
+            return fail(SB_ERR_INVALID_ARG, std::string(name) + ": levels must be in [1, 15]");
         const int64_t npx = (int64_t)f.tgt_guide.width * f.tgt_guide.height;
         if (npx > 0 && (!f.rgba8_out || ((uintptr_t)f.rgba8_out % 4)))
             return fail(SB_ERR_INVALID_ARG, std::string(name) + ": rgba8_out NULL or misaligned");
@@ -279,7 +347,11 @@ extern "C" sb_status sb_stylize_batch_sched(const sb_frame *frames, int32_t n_fr
     if (st != SB_OK || n_frames == 0 || b.tile_start[n_frames] == 0) return st;
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) return cuda_fail(e, "pending CUDA error");
-    e = launch_batch_any(channels, bits, b, blend_radius, sched.persistent != 0, max_levels,
+    TileQueue *queue = nullptr;
+    if (sched.persistent &&
+        (st = acquire_queue(static_cast<cudaStream_t>(stream), &queue)) != SB_OK)
+        return st;
+    e = launch_batch_any(channels, bits, b, blend_radius, queue, max_levels,
                          static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "sb_stylize_batch");
     return ok();

@@ -34,9 +34,9 @@ namespace sb {
 constexpr uint32_t kInvalid = 0xC000C000u;
 constexpr int kMaxSourceSide = 32767;         // keeps packed-position arithmetic carry-free
 constexpr int kMaxTargetSide = 65535;
-constexpr int kMaxLevels = 12;
+constexpr int kMaxLevels = 15;          // 2^15 = 32768 seed spacing
 constexpr int kMaxBlendRadius = 15;
-constexpr int kMaxFusedRadius = 7;
+constexpr int kMaxFusedRadius = 15;
 constexpr int kMaxKeyBitsTotal = 24;
 
 // error plumbing (host)

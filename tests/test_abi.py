@@ -94,7 +94,7 @@ def test_invalid_batch_and_schedule_arguments_are_rejected_on_the_host():
     best, ms = sb._Schedule(), ctypes.c_float()
     assert lib.sb_stylize_batch(frames, 129, 2, None) == -1            # too many frames
     assert lib.sb_stylize_batch(None, 1, 2, None) == -1                # NULL frames
-    assert lib.sb_stylize_batch_sched(frames, 1, 8, ctypes.byref(sched), None) == -1  # radius
+    assert lib.sb_stylize_batch_sched(frames, 1, 16, ctypes.byref(sched), None) == -1  # radius
     assert lib.sb_stylize_batch_sched(frames, -1, 2, None, None) == -1
     assert lib.sb_stylize_batch_sched(frames, 0, 2, None, None) == 0   # empty batch: no-op
     assert lib.sb_autotune_batch(frames, 1, 2, 3, None, ctypes.byref(ms), None) == -1  # no best

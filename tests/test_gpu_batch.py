@@ -81,9 +81,9 @@ def test_batch_argument_errors(cuda_device):
     f_ok = sb.BatchFrame(g8, exs[0][4], exs[0][3], 3, 100, 1)
     assert sb.stylize_batch([], 2) == []
     with pytest.raises(sb.StyleBlitError):
-        sb.stylize_batch([f_ok], 8)                                   # radius
+        sb.stylize_batch([f_ok], 16)                                  # radius above 15
     with pytest.raises(sb.StyleBlitError):
-        sb.stylize_batch([sb.BatchFrame(g8, exs[0][4], exs[0][3], 13, 1, 1)], 1)  # levels
+        sb.stylize_batch([sb.BatchFrame(g8, exs[0][4], exs[0][3], 16, 1, 1)], 1)  # levels above 15
     with pytest.raises(sb.StyleBlitError) as e:
         sb.stylize_batch([f_ok, sb.BatchFrame(g2, exs[0][4], exs[0][3], 3, 1, 1)], 1)
     assert e.value.status in (-1, -2)
@@ -168,7 +168,7 @@ def test_persistent_queue_resets_across_launches_and_graph_replays(cuda_device):
     frames = _uneven_batch(cuda_device, 6, 7)
     ref = [o.clone() for o in sb.stylize_batch(frames, 2)]
     sched = {"persistent": 1, "largest_first": 1}
-    for _ in range(70):  # more than the 64 queue slots
+    for _ in range(70):  # many launches on one stream reuse its queue
         sb.stylize_batch(frames, 2, schedule=sched)
     torch.cuda.synchronize()
     assert all(torch.equal(o, r) for o, r in zip([f.out for f in frames], ref))
@@ -182,6 +182,45 @@ def test_persistent_queue_resets_across_launches_and_graph_replays(cuda_device):
         graph.replay()
         torch.cuda.synchronize()
         assert all(torch.equal(f.out, r) for f, r in zip(frames, ref))
+
+
+def test_persistent_launches_on_unordered_streams_and_a_graph_never_share_a_queue(cuda_device):
+    """Persistent batches with radius 1 and radius 2 on four streams that do
+    not wait for each other (25 launches per stream, 100 in all), while a
+    captured persistent batch is replayed on a fifth stream: every launch
+    writes its own outputs and every output equals the one-CTA-per-tile
+    schedule's."""
+    sched = {"persistent": 1, "largest_first": 0}
+    inputs = {r: _uneven_batch(cuda_device, 2, 40 + r) for r in (1, 2)}
+    ref = {r: [o.clone() for o in sb.stylize_batch(inputs[r], r)] for r in (1, 2)}
+    streams = [torch.cuda.Stream(cuda_device) for _ in range(5)]
+    gframes = [sb.BatchFrame(f.tgt_guide, f.lut, f.style, f.levels, f.threshold, f.seed)
+               for f in inputs[2]]
+    with torch.cuda.stream(streams[4]):
+        sb.stylize_batch(gframes, 2, stream=streams[4], schedule=sched)  # set-up outside capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=streams[4]):
+        sb.stylize_batch(gframes, 2, stream=streams[4], schedule=sched)
+    torch.cuda.synchronize()
+    launches = []
+    for j in range(25):
+        for k, st in enumerate(streams[:4]):
+            r = 1 + k % 2
+            fr = [sb.BatchFrame(f.tgt_guide, f.lut, f.style, f.levels, f.threshold, f.seed)
+                  for f in inputs[r]]
+            with torch.cuda.stream(st):
+                sb.stylize_batch(fr, r, stream=st, schedule=sched)
+            launches.append((r, fr))
+        if j % 5 == 0:
+            with torch.cuda.stream(streams[4]):
+                for f in gframes:
+                    f.out.zero_()
+                graph.replay()
+    torch.cuda.synchronize()
+    for i, (r, fr) in enumerate(launches):
+        assert all(torch.equal(f.out, o) for f, o in zip(fr, ref[r])), f"launch {i} (r={r})"
+    assert all(torch.equal(f.out, o) for f, o in zip(gframes, ref[2]))
 
 
 def test_autotune_picks_a_schedule_and_keeps_the_pixels(cuda_device):

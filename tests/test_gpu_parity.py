@@ -94,7 +94,7 @@ def test_small_cases_bit_exact(cuda_device, name):
     assert np.array_equal(out, ref_out)
 
 
-@pytest.mark.parametrize("radius", [0, 1, 2, 3, 5, 7])
+@pytest.mark.parametrize("radius", [0, 1, 2, 3, 5, 7, 8, 11, 15])
 def test_workload_256_every_radius(cuda_device, radius):
     w = workload("256")
     ex, fr = w.exemplar, w.frames[0]
@@ -113,7 +113,10 @@ def test_workload_256_every_radius(cuda_device, radius):
     ((64, 32), 7, 400, 0xFFFFFFFF), ((31, 200), 3, 300, 12345),
     # level 8 (the largest level with packed seed keys) with every pixel falling
     # to level 1, level 8 with a mid threshold, level 9 (per-pixel lists)
-    ((300, 520), 8, 0, 77), ((97, 203), 8, 2000, 79), ((260, 300), 9, 500, 78)])
+    ((300, 520), 8, 0, 77), ((97, 203), 8, 2000, 79), ((260, 300), 9, 500, 78),
+    # the deepest hierarchies (spacing up to 2^15): on a 50000-pixel-wide target
+    # seed distances pass 2^31, so their squared distances need 64 bits
+    ((150, 700), 13, 150, 93), ((2, 50000), 15, 300, 91), ((3, 65535), 15, 0, 94)])
 def test_ragged_and_extreme_parameters(cuda_device, shape, levels, T, seed):
     H, W = shape
     tgt = synth.smooth_integer_guide(seed % 1000 + 1, H, W, 3, step=5)
@@ -147,7 +150,7 @@ def test_identity_uv_reproduces_the_exemplar(cuda_device):
     gd = to_dev(g, cuda_device)
     st = to_dev(style, cuda_device)
     lut = sb.build_lut(gd, 11)
-    for radius in (0, 3, 7):
+    for radius in (0, 3, 7, 15):
         out = sb.stylize(gd, gd, st, lut, 6, 0, radius, 77)
         assert np.array_equal(out.cpu().numpy(), style)
     a, lev = sb.assign_chunks(gd, gd, lut, 6, 0, 77)
@@ -374,14 +377,14 @@ def _random_case(seed):
                              high=int(rng.integers(1, high + 1)))
     style = synth.random_style(10 * seed + 3, Hs, Ws)
     T = int(rng.choice([0, int(rng.integers(0, 4 * high * high)), (1 << 64) - 1]))
-    return dict(tgt=tgt, src=src, style=style, kb=kb, kc=kc, levels=int(rng.integers(1, 10)),
-                T=T, r=int(rng.integers(0, 8)), seed=int(rng.integers(0, 2**32)))
+    return dict(tgt=tgt, src=src, style=style, kb=kb, kc=kc, levels=int(rng.integers(1, 16)),
+                T=T, r=int(rng.integers(0, 16)), seed=int(rng.integers(0, 2**32)))
 
 
 @pytest.mark.parametrize("seed", range(24))
 def test_randomized_configurations_match_oracle(cuda_device, seed):
     """Seeded random formats, sizes (ragged, tiny), key bits and keyed channels,
-    level counts, thresholds and radii: table, assignment, levels and RGBA8
+    level counts (1-15), thresholds and radii (0-15): table, assignment, levels and RGBA8
     output equal the oracle's."""
     c = _random_case(seed)
     gt, gs, st = to_dev(c["tgt"], cuda_device), to_dev(c["src"], cuda_device), to_dev(c["style"], cuda_device)
