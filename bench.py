@@ -61,6 +61,9 @@ def _args():
                    help="build the step's frames and launch sb_stylize_batch twice, then "
                         "sb_lookup_only_batch twice, no timing (a fixed launch sequence for ncu "
                         "captures)")
+    p.add_argument("--schedule", default="0,0,0",
+                   help="with --profile-once: the batch schedule as persistent,largest_first,"
+                        "interleave_rows (the bench line's config.schedule)")
     return p.parse_args()
 
 
@@ -370,8 +373,13 @@ def run_gpu(args):
     batch = [sb.BatchFrame(g_tgt[i], lut, style, w.levels, w.threshold, w.seed + i, out=outs[i])
              for i in range(FRAMES_PER_STEP)]
 
+    # the launch schedule: the one sb_autotune_batch picks for this batch
+    # (outputs are the same under every schedule)
+    tuned, _ = sb.autotune_batch(batch, w.blend_radius, reps=5, stream=stream)
+    torch.cuda.synchronize()
+
     def step_batch():
-        sb.stylize_batch(batch, w.blend_radius, stream=stream)
+        sb.stylize_batch(batch, w.blend_radius, stream=stream, schedule=tuned)
 
     def step_frames():
         for i in range(FRAMES_PER_STEP):
@@ -402,9 +410,6 @@ def run_gpu(args):
         barrier()
         return max_over_ranks(e0.elapsed_time(e1), world, dev)
 
-    def step_batch_persistent():
-        sb.stylize_batch(batch, w.blend_radius, stream=stream,
-                         schedule={"persistent": 1, "largest_first": 0})
 
     graph = capture(step_batch)
     graph_frames = capture(step_frames)
@@ -432,11 +437,20 @@ def run_gpu(args):
     value = job_throughput(world, px_step, args.steps, ms)
     pf_steps = max(3, min(args.steps, 300))
     ms_pf = time_graph(graph_frames, pf_steps)
-    graph_persistent = capture(step_batch_persistent)
-    for _ in range(3):
-        with torch.cuda.stream(stream):
-            graph_persistent.replay()
-    ms_persistent = time_graph(graph_persistent, pf_steps)
+    # every schedule of the same batch (one CTA per tile or persistent; frame
+    # order or tile rows interleaved across the frames)
+    by_schedule = {}
+    for pers in (0, 1):
+        for il in (0, 1):
+            sc = {"persistent": pers, "largest_first": 0, "interleave_rows": il}
+            gs_ = capture(lambda: sb.stylize_batch(batch, w.blend_radius, stream=stream,
+                                                   schedule=sc))
+            for _ in range(3):
+                with torch.cuda.stream(stream):
+                    gs_.replay()
+            by_schedule[f"persistent={pers},interleave_rows={il}"] = \
+                time_graph(gs_, pf_steps) / pf_steps
+            del gs_
 
     # the lookup-only comparator (Section 4, texture mapping) on the same frames:
     # one short launch per frame spread over four streams (forked from and
@@ -551,7 +565,9 @@ def run_gpu(args):
                        "l2": f"no flush: each step reads {step_bytes / 2**20:.0f} MiB of "
                              f"distinct guides and outputs (> {L2_BYTES // 2**20} MiB L2)",
                        "launch": "CUDA graph of one sb_stylize_batch launch over all "
-                                 "frames_per_step frames",
+                                 "frames_per_step frames, schedule picked by "
+                                 "sb_autotune_batch",
+                       "schedule": tuned,
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
@@ -575,11 +591,11 @@ def run_gpu(args):
                                 "alone, same streams (the host link's ceiling for e2e)"}},
             "issue_roofline": issue,
             "per_frame_launch": per_frame,
-            "persistent_schedule": {
-                "value": job_throughput(world, px_step, pf_steps, ms_persistent),
-                "unit": "Mpixel/s", "ms_per_step": ms_persistent / pf_steps, "steps": pf_steps,
-                "launch": "CUDA graph of one sb_stylize_batch launch, persistent work-queue "
-                          "schedule (one CTA per resident slot, tiles taken from a queue)"},
+            "schedules": {"autotuned": tuned, "ms_per_step": by_schedule,
+                          "what": "each a CUDA graph of one sb_stylize_batch launch over the "
+                                  "step's frames; persistent = resident CTAs taking tiles from "
+                                  "a work queue; interleave_rows = tile row r of every frame "
+                                  "before row r + 1"},
             "lookup_only": lookup,
             "gpu_launches": args.steps,
             "lut_build_ms": min(t_lut),
@@ -753,8 +769,17 @@ def run_workload_4k(dev, steps: int, warmup: int) -> dict:
             sb.stylize(gts[i], gs, st, lut, w.levels, w.threshold, w.blend_radius, w.seed + i,
                        out=outs[i], stream=stream)
 
-    ms_batch = timed(graph_of(lambda: sb.stylize_batch(batch, w.blend_radius, stream=stream)),
-                     steps)
+    tuned, _ = sb.autotune_batch(batch, w.blend_radius, reps=3, stream=stream)
+    torch.cuda.synchronize()
+    ms_batch = timed(graph_of(lambda: sb.stylize_batch(batch, w.blend_radius, stream=stream,
+                                                       schedule=tuned)), steps)
+    by_schedule = {}
+    for pers in (0, 1):
+        for il in (0, 1):
+            sc = {"persistent": pers, "largest_first": 0, "interleave_rows": il}
+            by_schedule[f"persistent={pers},interleave_rows={il}"] = timed(
+                graph_of(lambda: sb.stylize_batch(batch, w.blend_radius, stream=stream,
+                                                  schedule=sc)), max(10, steps // 3))
     ms_single = timed(graph_of(singles), max(3, steps // 2)) / FRAMES_PER_STEP
     lut.destroy()
     peaks = measured_peaks()
@@ -772,6 +797,7 @@ def run_workload_4k(dev, steps: int, warmup: int) -> dict:
             "blend": f"{2 * w.blend_radius + 1}x{2 * w.blend_radius + 1}",
             "value": job_throughput(1, FRAMES_PER_STEP * H * W, 1, ms_batch),
             "unit": "Mpixel/s", "ms_per_step": ms_batch, "steps": steps,
+            "schedule": tuned, "ms_per_step_by_schedule": by_schedule,
             "us_per_frame": 1e3 * ms_batch / FRAMES_PER_STEP,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
@@ -975,13 +1001,15 @@ def profile_once(args):
     lut = sb.build_lut(gs, ex.lut_bits)
     batch = [sb.BatchFrame(to_dev(f), lut, st, w.levels, w.threshold, w.seed + i)
              for i, f in enumerate(frames)]
+    pers, lf, il = (int(v) for v in args.schedule.split(","))
+    sched = {"persistent": pers, "largest_first": lf, "interleave_rows": il}
     for _ in range(2):
-        sb.stylize_batch(batch, w.blend_radius)
+        sb.stylize_batch(batch, w.blend_radius, schedule=sched)
     # then the lookup-only comparator over the same frames, batched, twice
     for _ in range(2):
         sb.lookup_only_batch(batch)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_once": w.name, "frames": len(batch)}))
+    print(json.dumps({"profile_once": w.name, "frames": len(batch), "schedule": sched}))
 
 
 def main():

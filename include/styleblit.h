@@ -101,17 +101,29 @@ typedef struct sb_lut sb_lut;
  * channels go through a distance transform over the grid of guide values,
  * the others through a pruned brute-force nearest-neighbour kernel.
  *
+ * Keys wider than 24 bits (e.g. four 8-bit channels at 7 or 8 bits, two
+ * 16-bit channels above 12 bits) get no table: the paper retrieves u* with
+ * search trees when more guide channels are used, and so does this library.
+ * The object then holds a search index (a two-level tree of guide-space boxes
+ * over 16 x 16-pixel tiles and 4 x 4-tile super-tiles) and the frame kernels
+ * query it for every seed at the seed's bin representative, which gives the
+ * same source position a full table would hold (exact nearest pixel, ties to
+ * the smallest y * width + x).  Such queries cost far more than a table read;
+ * sb_lookup_only refuses these objects (SB_ERR_UNSUPPORTED).
+ *
  *   src_guide  source guide G_S (device).  The table refers to positions in
  *              it; later calls must pass a source guide of the same size and
  *              format (checked) and the same content (not checked).
- *   key_bits   bits kept per channel, 1 <= key_bits <= bits and
- *              channels * key_bits <= 24 (at most 16 Mi entries, 64 MiB).
+ *   key_bits   bits kept per channel, 1 <= key_bits <= bits; a table for
+ *              channels * key_bits <= 24 (at most 16 Mi entries, 64 MiB), a
+ *              search index above.
  *   out        receives the new table; untouched on error.
  *   stream     the build is enqueued on this stream.  Temporary device
  *              memory is allocated and freed inside the call (stream-ordered):
  *              2 * 8 * 256^kc bytes for the distance transform (268 MB for
  *              three keyed channels), 16 bytes per 16x16 source tile for the
- *              search.
+ *              search.  A search index keeps its 16 bytes per tile (plus one
+ *              box per super-tile) for the object's lifetime.
  * Errors: SB_ERR_INVALID_ARG, SB_ERR_UNSUPPORTED, SB_ERR_OOM, SB_ERR_CUDA.
  */
 SB_API sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, sb_lut **out,
@@ -154,7 +166,8 @@ SB_API sb_status sb_lut_destroy(sb_lut *lut);
 /* Describes a table: device pointer to its 2^(key_channels*key_bits) uint32
  * entries (packed x | y << 16), entry count, channels and bits of the guide
  * it was built for, key_bits, key_channels, and that guide's width and height.
- * Any output pointer may be NULL. */
+ * A search index (keys wider than 24 bits) reports entries = NULL and
+ * n_entries = 0.  Any output pointer may be NULL. */
 SB_API sb_status sb_lut_info(const sb_lut *lut, const uint32_t **entries, int64_t *n_entries,
                              int32_t *channels, int32_t *bits, int32_t *key_bits,
                              int32_t *key_channels, int32_t *src_width, int32_t *src_height);
@@ -168,7 +181,8 @@ SB_API sb_status sb_lut_info(const sb_lut *lut, const uint32_t **entries, int64_
  * while the table maps the local guide to the source pixel nearest in those
  * key channels (ties to the smallest y * width + x).
  *
- *   key_channels  1..channels; key_channels * key_bits <= 24.
+ *   key_channels  1..channels; above 24 key bits a search index (as
+ *                 sb_build_lut) keyed on these channels.
  *   Other arguments, ownership and errors as sb_build_lut (which is this call
  *   with key_channels = channels).
  */
@@ -285,15 +299,22 @@ SB_API sb_status sb_stylize_batch(const sb_frame *frames, int32_t n_frames, int3
  *                  there fail with SB_ERR_UNSUPPORTED.
  *   largest_first  0: tiles in frame order; 1: frames with more tiles first
  *                  (shorter tail for uneven batches).
+ *   interleave_rows  0: each frame's tiles together; 1: when every frame of
+ *                  the batch has the same tile grid (64 x 32-pixel tiles),
+ *                  tile row r of every frame before tile row r + 1, so the
+ *                  exemplar lines those rows gather stay in L2 while the frames
+ *                  stream through; batches of frames with different tile grids
+ *                  keep frame order.
  */
 typedef struct {
     int32_t persistent;
     int32_t largest_first;
+    int32_t interleave_rows;
 } sb_batch_schedule;
 
 /*
  * sb_stylize_batch_sched -- sb_stylize_batch with an explicit schedule
- * (NULL: {0, 0}, the schedule of sb_stylize_batch).  Same arguments, outputs
+ * (NULL: {0, 0, 0}, the schedule of sb_stylize_batch).  Same arguments, outputs
  * and errors as sb_stylize_batch.
  */
 SB_API sb_status sb_stylize_batch_sched(const sb_frame *frames, int32_t n_frames,
@@ -302,7 +323,8 @@ SB_API sb_status sb_stylize_batch_sched(const sb_frame *frames, int32_t n_frames
 
 /*
  * sb_autotune_batch -- picks the fastest schedule for this batch (no
- * counterpart in the paper).  Runs each of the four schedules once untimed and
+ * counterpart in the paper).  Runs each schedule (persistent x largest_first,
+ * times interleave_rows when the frames share one tile grid) once untimed and
  * `reps` times between two CUDA events on `stream`, waits for the stream, and
  * writes the fastest to *best and its mean time per batch (ms) to *best_ms
  * (nullable).  The batch's outputs are written (every run writes the same

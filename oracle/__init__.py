@@ -157,9 +157,20 @@ def lut_size(channels: int, key_bits: int) -> int:
     return 1 << (channels * key_bits)
 
 
-def new_lut(channels: int, key_bits: int) -> np.ndarray:
-    """An empty table: every entry is computed on first use."""
+TABLE_MAX_KEY_BITS = 24
+
+
+def new_lut(channels: int, key_bits: int) -> np.ndarray | None:
+    """An empty table: every entry is computed on first use.  Keys wider than
+    24 bits get no table (None): every use computes the entry from its
+    definition."""
+    if channels * key_bits > TABLE_MAX_KEY_BITS:
+        return None
     return np.full(lut_size(channels, key_bits), UNSET, dtype=np.uint32)
+
+
+def _lut_ptr(lut):
+    return None if lut is None else _ptr(lut)
 
 
 def lut_index(guide: np.ndarray, x: int, y: int, key_bits: int, key_channels=None) -> int:
@@ -192,6 +203,8 @@ def build_lut(src_guide: np.ndarray, key_bits: int, n_threads: int = 0,
               key_channels=None) -> np.ndarray:
     g, keep = _guide(src_guide)
     kc = g.channels if key_channels is None else key_channels
+    if kc * key_bits > TABLE_MAX_KEY_BITS:
+        raise ValueError("keys wider than 24 bits have no table; use lut_entries")
     lut = np.empty(lut_size(kc, key_bits), dtype=np.uint32)
     _load().orc_build_lut(ctypes.byref(g), key_bits, kc, _ptr(lut), n_threads or os.cpu_count())
     return lut
@@ -211,7 +224,7 @@ def assign(tgt_guide, src_guide, key_bits, levels, threshold, seed, lut=None, n_
         lut = new_lut(kc, key_bits)
     a = np.empty((t.height, t.width), dtype=np.uint32)
     lev = np.empty((t.height, t.width), dtype=np.uint8)
-    _load().orc_assign(ctypes.byref(t), ctypes.byref(s), key_bits, kc, _ptr(lut), levels,
+    _load().orc_assign(ctypes.byref(t), ctypes.byref(s), key_bits, kc, _lut_ptr(lut), levels,
                        int(threshold), seed & 0xFFFFFFFF, _ptr(a), _ptr(lev), n_threads)
     return a, lev
 
@@ -227,7 +240,7 @@ def assign_points(tgt_guide, src_guide, key_bits, levels, threshold, seed, xs, y
     ys = np.ascontiguousarray(ys, dtype=np.int32)
     a = np.empty(len(xs), dtype=np.uint32)
     lev = np.empty(len(xs), dtype=np.uint8)
-    _load().orc_assign_points(ctypes.byref(t), ctypes.byref(s), key_bits, kc, _ptr(lut), levels,
+    _load().orc_assign_points(ctypes.byref(t), ctypes.byref(s), key_bits, kc, _lut_ptr(lut), levels,
                               int(threshold), seed & 0xFFFFFFFF, _ptr(xs), _ptr(ys), len(xs),
                               _ptr(a), _ptr(lev))
     return a, lev
@@ -273,7 +286,7 @@ def stylize_points(tgt_guide, src_guide, style, key_bits, levels, threshold, rad
     ys = np.ascontiguousarray(ys, dtype=np.int32)
     out = np.empty((len(xs), 4), dtype=np.uint8)
     _load().orc_stylize_points(ctypes.byref(t), ctypes.byref(s), ctypes.byref(st), key_bits,
-                               kc, _ptr(lut), levels, int(threshold), radius, seed & 0xFFFFFFFF,
+                               kc, _lut_ptr(lut), levels, int(threshold), radius, seed & 0xFFFFFFFF,
                                _ptr(xs), _ptr(ys), len(xs), _ptr(out))
     return out
 
@@ -288,5 +301,5 @@ def lookup_only(tgt_guide, src_guide, style, key_bits, lut=None, key_channels=No
         lut = new_lut(kc, key_bits)
     out = np.empty((t.height, t.width, 4), dtype=np.uint8)
     _load().orc_lookup_only(ctypes.byref(t), ctypes.byref(s), ctypes.byref(st), key_bits, kc,
-                            _ptr(lut), _ptr(out))
+                            _lut_ptr(lut), _ptr(out))
     return out

@@ -168,10 +168,14 @@ uint32_t orc_lut_entry(const orc_guide *src, int32_t key_bits, uint32_t idx)
 }
 
 /* A table entry, computed on first use.  Unfilled entries hold ORC_UNSET (no
- * valid entry has x = y = 65535 since source sides are at most 65535). */
+ * valid entry has x = y = 65535 since source sides are at most 65535).  With
+ * no table (keys too wide to tabulate, where the paper turns to search trees)
+ * the entry is computed from its definition at every use: the same value. */
 static uint32_t lut_lookup(uint32_t *lut, const orc_guide *src, int32_t key_bits,
                            int32_t key_channels, uint32_t idx)
 {
+    if (!lut)
+        return orc_lut_entry_k(src, key_bits, key_channels, idx);
     uint32_t v = __atomic_load_n(&lut[idx], __ATOMIC_RELAXED);
     if (v == ORC_UNSET) {
         v = orc_lut_entry_k(src, key_bits, key_channels, idx);

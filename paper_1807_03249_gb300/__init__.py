@@ -63,7 +63,8 @@ class _Rgba8(ctypes.Structure):
 
 
 class _Schedule(ctypes.Structure):
-    _fields_ = [("persistent", ctypes.c_int32), ("largest_first", ctypes.c_int32)]
+    _fields_ = [("persistent", ctypes.c_int32), ("largest_first", ctypes.c_int32),
+                ("interleave_rows", ctypes.c_int32)]
 
 
 class _Frame(ctypes.Structure):
@@ -210,8 +211,11 @@ class Lut:
 
     def entries(self) -> torch.Tensor:
         """A copy of the table (int32 bit patterns of x | y << 16), ordered on
-        the current stream after the work that built it."""
+        the current stream after the work that built it.  Keys wider than 24
+        bits have a search index instead of a table (ValueError here)."""
         info = self.info()
+        if not info["entries_ptr"]:
+            raise ValueError("this object holds a search index, not a table (key wider than 24 bits)")
         view = torch.as_tensor(_DeviceArray(info["entries_ptr"], info["n_entries"]),
                                device=self.device)
         return view.clone()
@@ -331,7 +335,8 @@ def _frames_array(frames):
 def stylize_batch(frames, radius: int, stream=None, schedule: dict | None = None):
     """Stylises up to MAX_BATCH frames (BatchFrame) in one launch; returns their
     outputs.  Frames share the guide format and the blend radius.  `schedule`
-    ({"persistent": 0/1, "largest_first": 0/1}, e.g. from autotune_batch)
+    ({"persistent": 0/1, "largest_first": 0/1, "interleave_rows": 0/1}, e.g.
+    from autotune_batch; missing keys are 0)
     picks the launch form; every schedule gives the same pixels."""
     lib = load_library()
     frames = list(frames)
@@ -339,7 +344,8 @@ def stylize_batch(frames, radius: int, stream=None, schedule: dict | None = None
     if schedule is None:
         _check("sb_stylize_batch", lib.sb_stylize_batch(arr, len(frames), radius, _stream(stream)))
     else:
-        sc = _Schedule(int(schedule.get("persistent", 0)), int(schedule.get("largest_first", 0)))
+        sc = _Schedule(int(schedule.get("persistent", 0)), int(schedule.get("largest_first", 0)),
+                       int(schedule.get("interleave_rows", 0)))
         _check("sb_stylize_batch_sched",
                lib.sb_stylize_batch_sched(arr, len(frames), radius, ctypes.byref(sc),
                                           _stream(stream)))
@@ -367,7 +373,8 @@ def autotune_batch(frames, radius: int, reps: int = 5, stream=None):
     _check("sb_autotune_batch", lib.sb_autotune_batch(arr, len(frames), radius, reps,
                                                       ctypes.byref(best), ctypes.byref(ms),
                                                       _stream(stream)))
-    return {"persistent": best.persistent, "largest_first": best.largest_first}, ms.value
+    return {"persistent": best.persistent, "largest_first": best.largest_first,
+            "interleave_rows": best.interleave_rows}, ms.value
 
 
 def stylize_batch_host(guides_host, luts, styles, levels, thresholds, seeds, radius: int,

@@ -45,6 +45,7 @@
 #include <climits>
 
 #include "sb_internal.cuh"
+#include "sb_nn.cuh"
 
 namespace sb {
 
@@ -68,7 +69,8 @@ struct FrameArgs {
     int W, H;
     const uint32_t *src_packed;  // G_S, one packed uint32 per pixel, row-major
     int Ws, Hs;
-    const uint32_t *lut;
+    const uint32_t *lut;         // table, or nullptr: query the search index
+    const uint4 *nn_bounds;      // search index (keys wider than 24 bits)
     int key_bits;
     int key_channels;
     const uint8_t *style;
@@ -235,6 +237,17 @@ __device__ __forceinline__ uint32_t biased_pos(int px, int py) {
     return (uint32_t)((px - kShiftBias) + (py - kShiftBias) * 65536);
 }
 
+// u*(q) of a seed whose target guide value is g (Algorithm 2, "found via
+// lookup"): the table entry of g's bin, or, for keys wider than a table, the
+// search index queried at the bin representative (the same source position).
+template <int C, int B>
+__device__ __forceinline__ uint32_t seed_source(const FrameArgs &a, uint32_t g) {
+    using F = GuideFmt<C, B>;
+    if (a.lut) return __ldg(a.lut + F::key(g, a.key_bits, a.key_channels));
+    return nn_query<C, B>(a.src_packed, a.nn_bounds, a.Ws, a.Hs,
+                          bin_representative<C, B>(g, a.key_bits, a.key_channels), a.key_channels);
+}
+
 // Builds cells k0, k0 + kThreads, ... of the levels l_hi down to l_lo into
 // cells[base_hi + k].
 template <int C, int B>
@@ -246,8 +259,7 @@ __device__ __forceinline__ void build_cells(const FrameArgs &a, int4 *cells, int
 #pragma unroll 1
     for (int k = k0 + (int)threadIdx.x; k < total; k += kThreads) {
         const CellTask t = cell_task(a, k, l_hi, xa, xb, ya, yb);
-        const uint32_t u = __ldg(
-            a.lut + F::key(F::load(a.tgt, a.tgt_stride, t.sx, t.sy), a.key_bits, a.key_channels));
+        const uint32_t u = seed_source<C, B>(a, F::load(a.tgt, a.tgt_stride, t.sx, t.sy));
         cells[base_hi + k] = cell_value(t, u, cxo, cyo);
     }
 }
@@ -559,7 +571,7 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
         }
     }
     uint32_t cu = 0;
-    if (has_cell) cu = __ldg(a.lut + F::key(cg, a.key_bits, a.key_channels));
+    if (has_cell) cu = seed_source<C, B>(a, cg);
 #pragma unroll
     for (int k = 0; k < kIt; ++k) {
         const int i = tid + k * kThreads;
@@ -867,55 +879,48 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
         }
         __syncthreads();
     }
-    // output rows: warp w takes rows w, w + 8, ...; a uniform window copies
+    // output rows: warp w takes rows w, w + 8, ...  A uniform window votes
+    // exactly C_S[A(p)] (all its taps share one source position; outside the
+    // source the vote is 0); the other pixels go to two block-wide lists, their
+    // membership read off warp-uniform 64-bit row masks.
     constexpr int kRowsPerWarp = kTH / kWarps;
+    const int wcols = min(a.W - x0, kTW);  // columns of the tile inside the target
+    const uint64_t incols = wcols >= 64 ? ~0ull : ((1ull << wcols) - 1ull);
     uint32_t col[kRowsPerWarp][2];
-    bool uni[kRowsPerWarp][2];
 #pragma unroll
     for (int q = 0; q < kRowsPerWarp; ++q) {
         const int ty = warp + q * kWarps;
         uint64_t U = ~0ull;
         if constexpr (R > 0) U = mk.U[ty];
+        if (y0 + ty >= a.H) U = 0;
+        U &= incols;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int tx = c * 32 + lane;
-            uni[q][c] = false;
             col[q][c] = 0;
-            if (x0 + tx < a.W && y0 + ty < a.H && ((U >> tx) & 1ull)) {
+            if ((U >> tx) & 1ull) {
                 const uint32_t v = A[(ty + R) * RW + tx + R];
-                uni[q][c] = sv.in_source(v);
-                if (uni[q][c]) col[q][c] = sv.at(v);
+                if (sv.in_source(v)) col[q][c] = sv.at(v);
             }
         }
     }
-    // stores of the copies; the other pixels go to two block-wide lists (a
-    // warp counts its entries with ballots, then reserves its ranges with one
-    // atomic per list)
-    unsigned mg[kRowsPerWarp][2], mt[kRowsPerWarp][2];
-    int n_g = 0, n_t = 0;
 #pragma unroll
     for (int q = 0; q < kRowsPerWarp; ++q) {
         const int ty = warp + q * kWarps;
-        uint64_t T2 = 0;
-        if constexpr (R > 0) T2 = mk.T2[ty];
+        uint64_t U = ~0ull;
+        if constexpr (R > 0) U = mk.U[ty];
+        if (y0 + ty >= a.H) U = 0;
+        U &= incols;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int tx = c * 32 + lane;
-            const bool in = x0 + tx < a.W && y0 + ty < a.H;
-            // R = 0: the only tap is p itself; outside the source it votes 0
-            if (uni[q][c] || (R == 0 && in)) {
+            if ((U >> tx) & 1ull) {
                 if constexpr (F32) {
-                    a.f32_out[(int64_t)(y0 + ty) * a.W + x0 + tx] = uni[q][c] ? rgba_f32(col[q][c]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    // outside the source col is 0, which votes (0, 0, 0, 0)
+                    a.f32_out[(int64_t)(y0 + ty) * a.W + x0 + tx] = rgba_f32(col[q][c]);
                 } else {
                     a.rgba_out[(int64_t)(y0 + ty) * a.W + x0 + tx] = col[q][c];
                 }
-            }
-            if constexpr (R > 0) {
-                const bool g = in && ((T2 >> tx) & 1ull);
-                mg[q][c] = __ballot_sync(0xFFFFFFFFu, g);
-                mt[q][c] = __ballot_sync(0xFFFFFFFFu, in && !uni[q][c] && !g);
-                n_g += __popc(mg[q][c]);
-                n_t += __popc(mt[q][c]);
             }
         }
     }
@@ -923,6 +928,17 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
         int *cnt = reinterpret_cast<int *>(smem + L.off_cnt);
         uint16_t *glist = reinterpret_cast<uint16_t *>(smem + L.off_list0);
         uint16_t *tlist = reinterpret_cast<uint16_t *>(smem + L.off_list1);
+        uint64_t Gm[kRowsPerWarp], Tm[kRowsPerWarp];
+        int n_g = 0, n_t = 0;
+#pragma unroll
+        for (int q = 0; q < kRowsPerWarp; ++q) {
+            const int ty = warp + q * kWarps;
+            const uint64_t in = y0 + ty < a.H ? incols : 0ull;
+            Gm[q] = mk.T2[ty] & in;
+            Tm[q] = ~mk.U[ty] & ~mk.T2[ty] & in;
+            n_g += __popcll(Gm[q]);
+            n_t += __popcll(Tm[q]);
+        }
         int bg = 0, bt = 0;
         if (lane == 0) {
             if (n_g) bg = atomicAdd(&cnt[3], n_g);
@@ -937,10 +953,11 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const int k = ty * kTW + c * 32 + lane;
-                if ((mg[q][c] >> lane) & 1u) glist[bg + __popc(mg[q][c] & lt)] = (uint16_t)k;
-                if ((mt[q][c] >> lane) & 1u) tlist[bt + __popc(mt[q][c] & lt)] = (uint16_t)k;
-                bg += __popc(mg[q][c]);
-                bt += __popc(mt[q][c]);
+                const uint32_t mg = (uint32_t)(Gm[q] >> (32 * c)), mt = (uint32_t)(Tm[q] >> (32 * c));
+                if ((mg >> lane) & 1u) glist[bg + __popc(mg & lt)] = (uint16_t)k;
+                if ((mt >> lane) & 1u) tlist[bt + __popc(mt & lt)] = (uint16_t)k;
+                bg += __popc(mg);
+                bt += __popc(mt);
             }
         }
         __syncthreads();
@@ -997,15 +1014,30 @@ constexpr int kMaxBatch = 128;
 
 struct BatchArgs {
     int n;
+    // tile order: 0 frame by frame; otherwise (every frame has rows_tx x
+    // rows_ty tiles) tile row r of every frame before tile row r + 1, so the
+    // exemplar lines those rows gather stay in L2 across the frames
+    int rows_interleaved;
+    int rows_tx;
     int tile_start[kMaxBatch + 1];
     int tiles_x[kMaxBatch];
     FrameArgs f[kMaxBatch];
 };
 
-// Tile t of a batch: the frame k with tile_start[k] <= t < tile_start[k + 1].
+// Tile t of a batch: the frame k with tile_start[k] <= t < tile_start[k + 1]
+// (frame by frame), or tile row t / (n * rows_tx) of frame (t / rows_tx) % n
+// (rows interleaved).
 template <int C, int B, int R>
 __device__ __forceinline__ void batch_tile(const BatchArgs &b, const SmemLayout &L, int t,
                                            unsigned char *smem) {
+    if (b.rows_interleaved) {
+        const int per_row = b.n * b.rows_tx;
+        const int r = t / per_row, rem = t - r * per_row;
+        const int k = rem / b.rows_tx;
+        const FrameArgs a = b.f[k];
+        frame_tile<C, B, kStylize, R>(a, L, rem - k * b.rows_tx, r, smem);
+        return;
+    }
     int lo = 0, hi = b.n - 1;  // last frame whose first tile is <= t
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;

@@ -175,6 +175,7 @@ static FrameArgs frame_args(const sb_guide *tgt, const sb_lut *lut, int32_t leve
     a.Ws = lut->src_w;
     a.Hs = lut->src_h;
     a.lut = lut->entries;
+    a.nn_bounds = lut->nn_bounds;
     a.key_bits = lut->key_bits;
     a.key_channels = lut->key_channels;
     a.levels = levels;
@@ -271,8 +272,8 @@ extern "C" sb_status sb_blend(const uint32_t *assign, int32_t tgt_w, int32_t tgt
 // order or, with largest_first, by decreasing tile count (each frame keeps its
 // own output, so the order changes only which tiles are issued first).
 static sb_status prepare_batch(const sb_frame *frames, int32_t n_frames, int32_t blend_radius,
-                               bool largest_first, BatchArgs &b, int &max_levels,
-                               int &channels, int &bits) {
+                               bool largest_first, bool interleave_rows, BatchArgs &b,
+                               int &max_levels, int &channels, int &bits) {
     if (n_frames < 0 || n_frames > kMaxBatch)
         return fail(SB_ERR_INVALID_ARG, "n_frames must be in [0, 128]");
     if (n_frames == 0) return ok();
@@ -280,6 +281,8 @@ static sb_status prepare_batch(const sb_frame *frames, int32_t n_frames, int32_t
     if (blend_radius < 0 || blend_radius > kMaxFusedRadius)
         return fail(SB_ERR_INVALID_ARG, "blend_radius must be in [0, 15]");
     b.n = n_frames;
+    b.rows_interleaved = 0;
+    b.rows_tx = 0;
     b.tile_start[0] = 0;
     max_levels = 1;
     channels = frames[0].tgt_guide.channels;
@@ -328,6 +331,19 @@ static sb_status prepare_batch(const sb_frame *frames, int32_t n_frames, int32_t
         a.rgba_out = reinterpret_cast<uint32_t *>(f.rgba8_out);
         b.f[i] = a;
     }
+    // rows interleaved only when every frame has the same tile grid
+    if (interleave_rows) {
+        const int tx0 = (frames[0].tgt_guide.width + kTW - 1) / kTW;
+        const int ty0 = (frames[0].tgt_guide.height + kTH - 1) / kTH;
+        bool same = tiles[0] > 0;
+        for (int k = 1; k < n_frames && same; ++k)
+            same = (frames[k].tgt_guide.width + kTW - 1) / kTW == tx0 &&
+                   (frames[k].tgt_guide.height + kTH - 1) / kTH == ty0 && tiles[k] > 0;
+        if (same) {
+            b.rows_interleaved = 1;
+            b.rows_tx = tx0;
+        }
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     for (int k = 0; k < n_frames; ++k)
@@ -339,11 +355,11 @@ extern "C" sb_status sb_stylize_batch_sched(const sb_frame *frames, int32_t n_fr
                                             int32_t blend_radius,
                                             const sb_batch_schedule *schedule,
                                             sb_stream stream) {
-    const sb_batch_schedule sched = schedule ? *schedule : sb_batch_schedule{0, 0};
+    const sb_batch_schedule sched = schedule ? *schedule : sb_batch_schedule{0, 0, 0};
     static thread_local BatchArgs b;  // ~18 KB: kept off the stack
     int max_levels = 1, channels = 0, bits = 0;
-    sb_status st = prepare_batch(frames, n_frames, blend_radius, sched.largest_first != 0, b,
-                                 max_levels, channels, bits);
+    sb_status st = prepare_batch(frames, n_frames, blend_radius, sched.largest_first != 0,
+                                 sched.interleave_rows != 0, b, max_levels, channels, bits);
     if (st != SB_OK || n_frames == 0 || b.tile_start[n_frames] == 0) return st;
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) return cuda_fail(e, "pending CUDA error");
@@ -374,7 +390,19 @@ extern "C" sb_status sb_autotune_batch(const sb_frame *frames, int32_t n_frames,
     if (e != cudaSuccess) return cuda_fail(e, "sb_autotune_batch");
     if (cap != cudaStreamCaptureStatusNone)
         return fail(SB_ERR_INVALID_ARG, "sb_autotune_batch: the stream is being captured");
-    const sb_batch_schedule cand[4] = {{0, 0}, {0, 1}, {1, 0}, {1, 1}};
+    // every combination of the three choices; interleaving rows is tried only
+    // when the frames share one tile grid (otherwise it is frame order again)
+    bool same_grid = n_frames > 0 && n_frames <= kMaxBatch && frames;
+    for (int k = 1; k < n_frames && same_grid; ++k)
+        same_grid = (frames[k].tgt_guide.width + kTW - 1) / kTW ==
+                        (frames[0].tgt_guide.width + kTW - 1) / kTW &&
+                    (frames[k].tgt_guide.height + kTH - 1) / kTH ==
+                        (frames[0].tgt_guide.height + kTH - 1) / kTH;
+    sb_batch_schedule cand[8];
+    int n_cand = 0;
+    for (int il = 0; il <= (same_grid ? 1 : 0); ++il)
+        for (int pers = 0; pers <= 1; ++pers)
+            for (int lf = 0; lf <= 1; ++lf) cand[n_cand++] = sb_batch_schedule{pers, lf, il};
     cudaEvent_t ev[2];
     if ((e = cudaEventCreate(&ev[0])) != cudaSuccess) return cuda_fail(e, "sb_autotune_batch");
     if ((e = cudaEventCreate(&ev[1])) != cudaSuccess) {
@@ -384,7 +412,7 @@ extern "C" sb_status sb_autotune_batch(const sb_frame *frames, int32_t n_frames,
     sb_status st = SB_OK;
     float best_t = 0.f;
     int best_i = 0;
-    for (int i = 0; i < 4 && st == SB_OK; ++i) {
+    for (int i = 0; i < n_cand && st == SB_OK; ++i) {
         // one untimed run, then reps timed runs between two events
         st = sb_stylize_batch_sched(frames, n_frames, blend_radius, &cand[i], stream);
         if (st == SB_OK) e = cudaEventRecord(ev[0], s);

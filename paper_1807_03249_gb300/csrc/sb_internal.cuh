@@ -13,7 +13,11 @@
 #include "styleblit.h"
 
 struct sb_lut {
-    uint32_t *entries = nullptr;   // device, 2^(channels*key_bits) packed x | y << 16
+    // table: 2^(key_channels * key_bits) entries packed x | y << 16, for keys
+    // of at most 24 bits; wider keys: nullptr, and nn_bounds holds the search
+    // index (tile and super-tile guide boxes) queried per seed
+    uint32_t *entries = nullptr;
+    uint4 *nn_bounds = nullptr;
     uint32_t *src_packed = nullptr;  // device, the source guide, one packed uint32 per pixel
     int64_t n_entries = 0;
     int32_t channels = 0;
@@ -37,7 +41,7 @@ constexpr int kMaxTargetSide = 65535;
 constexpr int kMaxLevels = 15;          // 2^15 = 32768 seed spacing
 constexpr int kMaxBlendRadius = 15;
 constexpr int kMaxFusedRadius = 15;
-constexpr int kMaxKeyBitsTotal = 24;
+constexpr int kMaxKeyBitsTotal = 24;        // widest key with a table (16 Mi entries)
 
 // error plumbing (host)
 sb_status fail(sb_status st, const std::string &msg);

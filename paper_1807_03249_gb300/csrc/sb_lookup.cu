@@ -215,6 +215,8 @@ extern "C" sb_status sb_lookup_only(const sb_guide *tgt_guide, const sb_guide *s
     if (tgt_guide->channels != src_guide->channels || tgt_guide->bits != src_guide->bits)
         return fail(SB_ERR_INVALID_ARG, "target and source guides differ in channels or bits");
     if (!lut) return fail(SB_ERR_INVALID_ARG, "lut: NULL");
+    if (!lut->entries)
+        return fail(SB_ERR_UNSUPPORTED, "sb_lookup_only needs a table (keys of at most 24 bits)");
     if (lut->channels != src_guide->channels || lut->bits != src_guide->bits ||
         lut->src_w != src_guide->width || lut->src_h != src_guide->height)
         return fail(SB_ERR_INVALID_ARG, "lut was built for a different source guide format/size");
@@ -261,6 +263,9 @@ extern "C" sb_status sb_lookup_only_batch(const sb_frame *frames, int32_t n_fram
                         "sb_lookup_only_batch: frames must share one guide format");
         std::snprintf(name, sizeof name, "frames[%d]", k);
         if (!f.lut) return fail(SB_ERR_INVALID_ARG, std::string(name) + ": lut NULL");
+        if (!f.lut->entries)
+            return fail(SB_ERR_UNSUPPORTED,
+                        std::string(name) + ": sb_lookup_only needs a table (keys of at most 24 bits)");
         if (f.lut->channels != channels || f.lut->bits != bits)
             return fail(SB_ERR_INVALID_ARG, std::string(name) + ": lut built for another format");
         std::snprintf(name, sizeof name, "frames[%d].src_style", k);

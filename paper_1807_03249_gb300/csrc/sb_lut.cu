@@ -18,11 +18,10 @@
 #include <algorithm>
 #include <cstdio>
 
-#include "sb_internal.cuh"
+#include "sb_nn.cuh"
 
 namespace sb {
 
-constexpr int kLutTile = 16;
 constexpr int kLutThreads = 256;
 
 // One packed uint32 per source pixel (the layout GuideFmt::load returns), so
@@ -86,7 +85,6 @@ __global__ void __launch_bounds__(256) lut_tile_bounds_kernel(const uint8_t *__r
 
 // Boxes of super-tiles (kSuper x kSuper tiles): the union of their tiles'
 // boxes, stored after the n_tiles tile boxes.
-constexpr int kSuper = 4;
 
 template <int C>
 __global__ void __launch_bounds__(256) lut_super_bounds_kernel(uint4 *__restrict__ bounds,
@@ -111,21 +109,6 @@ __global__ void __launch_bounds__(256) lut_super_bounds_kernel(uint4 *__restrict
 #pragma unroll
     for (int c = 0; c < C; ++c) w[c] = mn[c] | (mx[c] << 16);
     bounds[n_tiles + st] = make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-// squared distance from a representative to a tile's guide box
-template <int C, int B>
-__device__ __forceinline__ uint64_t box_distance(const uint32_t (&rep)[C], uint4 bb, int kc) {
-    const uint32_t w[4] = {bb.x, bb.y, bb.z, bb.w};
-    uint64_t lb = 0;
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        if (c >= kc) break;
-        const uint32_t lo = w[c] & 0xFFFFu, hi = w[c] >> 16;
-        const uint32_t t = rep[c] < lo ? lo - rep[c] : (rep[c] > hi ? rep[c] - hi : 0u);
-        lb += (uint64_t)t * t;
-    }
-    return lb;
 }
 
 // Source-guide readers for the search: the packed copy owned by an sb_lut,
@@ -372,6 +355,66 @@ struct LutLaunch {
     }
 };
 
+// The search index of a source guide (keys wider than 24 bits): the packed
+// guide and the tile and super-tile guide boxes.
+struct IndexLaunch {
+    const sb_guide *src;
+    uint32_t *packed;
+    uint4 *bounds;
+    cudaStream_t stream;
+    template <int C, int B>
+    void operator()() {
+        const NnGeometry g = NnGeometry::of(src->width, src->height);
+        const uint8_t *p = static_cast<const uint8_t *>(src->data);
+        const int64_t n_px = (int64_t)src->width * src->height;
+        pack_guide_kernel<C, B><<<(unsigned)((n_px + 255) / 256), 256, 0, stream>>>(
+            p, src->row_stride, src->width, src->height, packed);
+        lut_tile_bounds_kernel<C, B><<<(g.n_tiles + 7) / 8, 256, 0, stream>>>(
+            p, src->row_stride, src->width, src->height, g.tiles_x, g.n_tiles, bounds);
+        lut_super_bounds_kernel<C><<<(g.n_supers + 255) / 256, 256, 0, stream>>>(
+            bounds, g.tiles_x, g.tiles_y, g.n_tiles, g.supers_x, g.n_supers);
+    }
+};
+
+// sb_build_lut_keyed for keys wider than 24 bits: no table; the frame
+// kernels query the search index for every seed.
+static sb_status build_search_index(const sb_guide *src, int32_t key_bits, int32_t key_channels,
+                                    sb_lut **out, cudaStream_t s) {
+    const NnGeometry g = NnGeometry::of(src->width, src->height);
+    sb_lut *lut = new sb_lut;
+    lut->key_channels = key_channels;
+    lut->n_entries = 0;
+    lut->channels = src->channels;
+    lut->bits = src->bits;
+    lut->key_bits = key_bits;
+    lut->src_w = src->width;
+    lut->src_h = src->height;
+    cudaGetDevice(&lut->device);
+    cudaError_t e;
+    const size_t n_px = (size_t)src->width * src->height;
+    if ((e = cudaMalloc(&lut->src_packed, sizeof(uint32_t) * n_px)) != cudaSuccess) {
+        delete lut;
+        return cuda_fail(e, "sb_build_lut: packed guide allocation");
+    }
+    if ((e = cudaMalloc(&lut->nn_bounds, sizeof(uint4) * (size_t)(g.n_tiles + g.n_supers))) !=
+        cudaSuccess) {
+        cudaFree(lut->src_packed);
+        delete lut;
+        return cuda_fail(e, "sb_build_lut: search index allocation");
+    }
+    IndexLaunch L{src, lut->src_packed, lut->nn_bounds, s};
+    dispatch_format(src->channels, src->bits, L);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        cudaFree(lut->src_packed);
+        cudaFree(lut->nn_bounds);
+        delete lut;
+        return cuda_fail(e, "sb_build_lut: launch");
+    }
+    *out = lut;
+    return ok();
+}
+
 }  // namespace sb
 
 using namespace sb;
@@ -385,11 +428,11 @@ extern "C" sb_status sb_build_lut_keyed(const sb_guide *src_guide, int32_t key_b
         return fail(SB_ERR_INVALID_ARG, "key_bits must be in [1, bits]");
     if (key_channels < 1 || key_channels > src_guide->channels)
         return fail(SB_ERR_INVALID_ARG, "key_channels must be in [1, channels]");
-    if (key_channels * key_bits > kMaxKeyBitsTotal)
-        return fail(SB_ERR_INVALID_ARG, "key_channels * key_bits must be <= 24");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) return cuda_fail(e, "sb_build_lut: pending CUDA error");
+    if (key_channels * key_bits > kMaxKeyBitsTotal)
+        return build_search_index(src_guide, key_bits, key_channels, out, s);
 
     const uint32_t n_bins = 1u << (key_channels * key_bits);
     const int tiles_x = (src_guide->width + kLutTile - 1) / kLutTile;
@@ -447,18 +490,17 @@ extern "C" sb_status sb_build_lut_keyed(const sb_guide *src_guide, int32_t key_b
 
 extern "C" sb_status sb_build_lut(const sb_guide *src_guide, int32_t key_bits, sb_lut **out,
                                   sb_stream stream) {
-    const int32_t channels = src_guide ? src_guide->channels : 0;
     if (!src_guide) return fail(SB_ERR_INVALID_ARG, "src_guide: NULL guide descriptor");
-    if (channels >= 1 && channels * key_bits > kMaxKeyBitsTotal && key_bits >= 1)
-        return fail(SB_ERR_INVALID_ARG, "channels * key_bits must be <= 24");
-    return sb_build_lut_keyed(src_guide, key_bits, channels, out, stream);
+    return sb_build_lut_keyed(src_guide, key_bits, src_guide->channels, out, stream);
 }
 
 extern "C" sb_status sb_lut_destroy(sb_lut *lut) {
     if (!lut) return ok();
     cudaError_t e = cudaFree(lut->entries);
     cudaError_t e2 = cudaFree(lut->src_packed);
+    cudaError_t e3 = cudaFree(lut->nn_bounds);
     if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = e3;
     delete lut;
     if (e != cudaSuccess) return cuda_fail(e, "sb_lut_destroy");
     return ok();

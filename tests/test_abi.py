@@ -81,7 +81,8 @@ def test_invalid_blend_and_lut_arguments_are_rejected_on_the_host():
     assert lib.sb_build_lut(ctypes.byref(g), 0, ctypes.byref(h), None) == -1
     assert lib.sb_build_lut(ctypes.byref(g), 9, ctypes.byref(h), None) == -1
     g4 = _guide(32, 32, 4, 8)
-    assert lib.sb_build_lut(ctypes.byref(g4), 7, ctypes.byref(h), None) == -1  # 28 key bits
+    assert lib.sb_build_lut_keyed(ctypes.byref(g4), 7, 5, ctypes.byref(h), None) == -1  # 5 > 4 channels
+    assert lib.sb_build_lut_keyed(ctypes.byref(g4), 7, 0, ctypes.byref(h), None) == -1  # no channel
     assert lib.sb_build_lut(None, 6, ctypes.byref(h), None) == -1
     assert h.value is None
     assert lib.sb_lut_destroy(None) == 0
@@ -90,7 +91,7 @@ def test_invalid_blend_and_lut_arguments_are_rejected_on_the_host():
 def test_invalid_batch_and_schedule_arguments_are_rejected_on_the_host():
     lib = sb.load_library()
     frames = (sb._Frame * 1)()
-    sched = sb._Schedule(1, 1)
+    sched = sb._Schedule(1, 1, 0)
     best, ms = sb._Schedule(), ctypes.c_float()
     assert lib.sb_stylize_batch(frames, 129, 2, None) == -1            # too many frames
     assert lib.sb_stylize_batch(None, 1, 2, None) == -1                # NULL frames

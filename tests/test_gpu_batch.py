@@ -155,10 +155,43 @@ def test_every_schedule_gives_the_same_pixels(cuda_device, radius):
                 f.out.zero_()
             outs = sb.stylize_batch(frames, radius,
                                     schedule={"persistent": persistent,
-                                              "largest_first": largest_first})
+                                              "largest_first": largest_first,
+                                              "interleave_rows": 1})  # mixed grids: frame order
             torch.cuda.synchronize()
             for k, (o, r) in enumerate(zip(outs, ref)):
                 assert torch.equal(o, r), f"schedule {persistent}{largest_first} frame {k}"
+
+
+@pytest.mark.parametrize("radius", [2, 3])
+def test_interleaved_tile_rows_give_the_same_pixels(cuda_device, radius):
+    """Frames sharing one tile grid (different sizes inside the same 64 x 32
+    tiling, exemplars, levels and seeds) with their tile rows interleaved,
+    one CTA per tile and persistent: every frame equals the frame-order
+    launch and the oracle."""
+    rng = np.random.default_rng(60 + radius)
+    exs = _exemplars(cuda_device, 3)
+    frames, hosts = [], []
+    for k in range(6):
+        W, H = 256 - int(rng.integers(0, 60)), 150 - int(rng.integers(0, 20))  # 4 x 5 tiles each
+        g = synth.bump_normals(1500 + k, H, W, 3, (6.0, 40.0))
+        e = exs[k % 3]
+        levels, T, seed = int(rng.integers(2, 8)), int(rng.integers(50, 2000)), int(rng.integers(0, 2**32))
+        frames.append(sb.BatchFrame(to_dev(g, cuda_device), e[4], e[3], levels, T, seed))
+        hosts.append((g, e, levels, T, seed))
+    ref = [o.clone() for o in sb.stylize_batch(frames, radius)]
+    for persistent in (0, 1):
+        for f in frames:
+            f.out.zero_()
+        outs = sb.stylize_batch(frames, radius, schedule={"persistent": persistent,
+                                                          "interleave_rows": 1})
+        torch.cuda.synchronize()
+        assert all(torch.equal(o, r) for o, r in zip(outs, ref)), f"persistent={persistent}"
+    for k in (0, 3):
+        g, e, levels, T, seed = hosts[k]
+        want, _, _ = oracle.stylize(g, e[0], e[1], 5, levels, T, radius, seed)
+        assert np.array_equal(ref[k].cpu().numpy(), want)
+    best, _ = sb.autotune_batch(frames, radius, reps=1)
+    assert set(best) == {"persistent", "largest_first", "interleave_rows"}
 
 
 def test_persistent_queue_resets_across_launches_and_graph_replays(cuda_device):

@@ -289,6 +289,46 @@ def test_lookup_only_full_size_sampled(cuda_device):
 
 
 # ---------------------------------------------------------------------------
+# keys too wide for a table: the search index (Section 3.1, search trees for
+# more guide channels)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("channels,bits,key_bits,radius", [
+    (4, 8, 8, 2), (4, 8, 7, 0), (2, 16, 16, 3), (2, 16, 13, 1)])
+def test_wide_keys_search_index_matches_oracle(cuda_device, channels, bits, key_bits, radius):
+    """Keys of 28-32 bits get a search index instead of a table; every seed's
+    u* is then an exact nearest-pixel query.  Assignment, levels and RGBA8
+    output (single frame and batched) equal the oracle's, which computes each
+    u* from its definition."""
+    tgt = synth.smooth_integer_guide(80 + key_bits, 70, 150, channels, step=5)
+    src = synth.smooth_integer_guide(90 + key_bits, 45, 61, channels, step=5)
+    if bits == 16:
+        tgt = tgt.astype(np.uint16) * 257 + 5
+        src = src.astype(np.uint16) * 257
+    style = synth.random_style(95, 45, 61)
+    gt, gs, st = to_dev(tgt, cuda_device), to_dev(src, cuda_device), to_dev(style, cuda_device)
+    lut = sb.build_lut(gs, key_bits)
+    info = lut.info()
+    assert info["entries_ptr"] is None or info["entries_ptr"] == 0
+    assert info["n_entries"] == 0
+    levels, T, seed = 5, 300 if bits == 8 else 1 << 21, 4242
+    a, lev = sb.assign_chunks(gt, gs, lut, levels, T, seed)
+    out = sb.stylize(gt, gs, st, lut, levels, T, radius, seed)
+    bout = sb.stylize_batch([sb.BatchFrame(gt, lut, st, levels, T, seed)], radius)[0]
+    torch.cuda.synchronize()
+    ref_out, ref_a, ref_lev = oracle.stylize(tgt, src, style, key_bits, levels, T, radius, seed,
+                                             n_threads=4)
+    assert np.array_equal(u32(a), ref_a) and np.array_equal(lev.cpu().numpy(), ref_lev)
+    assert np.array_equal(out.cpu().numpy(), ref_out)
+    assert torch.equal(bout, out)
+    with pytest.raises(sb.StyleBlitError) as e:
+        sb.lookup_only(gt, gs, st, lut)
+    assert e.value.status == -2
+    with pytest.raises(ValueError):
+        lut.entries()
+
+
+# ---------------------------------------------------------------------------
 # extra guide channels (Section 4 segmentation guide): table keyed on the local guide
 # ---------------------------------------------------------------------------
 

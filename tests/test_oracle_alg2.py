@@ -120,6 +120,23 @@ def _guide_dist(GS, GT, a):
     return ((s - GT.astype(np.int64)) ** 2).sum(axis=-1)
 
 
+@pytest.mark.parametrize("channels,bits,T,seed", [(4, 8, 300, 4), (2, 16, 1 << 20, 9)])
+def test_wide_keys_without_a_table_match_literal_algorithm2(channels, bits, T, seed):
+    """Keys too wide for a table (4 x 8 and 2 x 16 bits, lossless): the oracle
+    computes u* from its definition at every seed, which must equal the
+    transcription's brute-force argmin."""
+    GT = synth.smooth_integer_guide(40 + seed, 17, 22, channels, step=5)
+    GS = synth.smooth_integer_guide(50 + seed, 11, 13, channels, step=5)
+    if bits == 16:  # spread over 16 bits (and off the multiples of 257 for the target)
+        GT = GT.astype(np.uint16) * 257 + 3
+        GS = GS.astype(np.uint16) * 257
+    assert oracle.new_lut(channels, bits) is None
+    A_ref, lev_ref = _parallel_styleblit(GT, GS, T, 4, seed)
+    a, lev = oracle.assign(GT, GS, bits, 4, T, seed)
+    assert np.array_equal(_unpack(a), A_ref)
+    assert np.array_equal(lev, lev_ref)
+
+
 def test_accepted_candidates_satisfy_threshold_normals():
     w = synth.workload_256()
     ex, fr = w.exemplar, w.frames[0]

@@ -79,7 +79,9 @@ def test_exact_hits_take_the_first_pixel_in_raster_order():
 
 @pytest.mark.parametrize("channels,bits,key_bits,shape", [
     (3, 8, 4, (24, 20)), (2, 8, 5, (17, 31)), (2, 16, 6, (16, 16)), (1, 8, 8, (7, 5)),
-    (4, 8, 3, (12, 12))])
+    (4, 8, 3, (12, 12)),
+    # keys wider than a table (the paper's search-tree case): 28 and 32 bits
+    (4, 8, 7, (9, 11)), (4, 8, 8, (12, 14)), (2, 16, 16, (10, 12))])
 def test_min_distance_matches_kdtree(channels, bits, key_bits, shape):
     spatial = pytest.importorskip("scipy.spatial")
     H, W = shape
