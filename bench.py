@@ -61,9 +61,9 @@ def _args():
                    help="build the step's frames and launch sb_stylize_batch twice, then "
                         "sb_lookup_only_batch twice, no timing (a fixed launch sequence for ncu "
                         "captures)")
-    p.add_argument("--schedule", default="0,0,0",
+    p.add_argument("--schedule", default="0,0,0,0",
                    help="with --profile-once: the batch schedule as persistent,largest_first,"
-                        "interleave_rows (the bench line's config.schedule)")
+                        "interleave_rows,tile_rows (the bench line's config.schedule)")
     return p.parse_args()
 
 
@@ -133,7 +133,7 @@ def kernel_source_hash() -> str:
     d = os.path.join(ROOT, "paper_1807_03249_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(d)):
-        if f in ("sb_frame.cuh", "sb_internal.cuh") or (f.startswith("sb_frame_c") and f.endswith(".cu")):
+        if f in ("sb_frame.cuh", "sb_internal.cuh", "sb_nn.cuh") or (f.startswith("sb_frame_c") and f.endswith(".cu")):
             h.update(_code_only(open(os.path.join(d, f)).read()).encode())
     return h.hexdigest()[:16]
 
@@ -440,17 +440,19 @@ def run_gpu(args):
     # every schedule of the same batch (one CTA per tile or persistent; frame
     # order or tile rows interleaved across the frames)
     by_schedule = {}
-    for pers in (0, 1):
-        for il in (0, 1):
-            sc = {"persistent": pers, "largest_first": 0, "interleave_rows": il}
-            gs_ = capture(lambda: sb.stylize_batch(batch, w.blend_radius, stream=stream,
-                                                   schedule=sc))
-            for _ in range(3):
-                with torch.cuda.stream(stream):
-                    gs_.replay()
-            by_schedule[f"persistent={pers},interleave_rows={il}"] = \
-                time_graph(gs_, pf_steps) / pf_steps
-            del gs_
+    for rows in (32, 16, 64):
+        for pers in (0, 1):
+            for il in (0, 1):
+                sc = {"persistent": pers, "largest_first": 0, "interleave_rows": il,
+                      "tile_rows": rows}
+                gs_ = capture(lambda: sb.stylize_batch(batch, w.blend_radius, stream=stream,
+                                                       schedule=sc))
+                for _ in range(3):
+                    with torch.cuda.stream(stream):
+                        gs_.replay()
+                by_schedule[f"tile_rows={rows},persistent={pers},interleave_rows={il}"] = \
+                    time_graph(gs_, pf_steps) / pf_steps
+                del gs_
 
     # the lookup-only comparator (Section 4, texture mapping) on the same frames:
     # one short launch per frame spread over four streams (forked from and
@@ -774,12 +776,14 @@ def run_workload_4k(dev, steps: int, warmup: int) -> dict:
     ms_batch = timed(graph_of(lambda: sb.stylize_batch(batch, w.blend_radius, stream=stream,
                                                        schedule=tuned)), steps)
     by_schedule = {}
-    for pers in (0, 1):
-        for il in (0, 1):
-            sc = {"persistent": pers, "largest_first": 0, "interleave_rows": il}
-            by_schedule[f"persistent={pers},interleave_rows={il}"] = timed(
-                graph_of(lambda: sb.stylize_batch(batch, w.blend_radius, stream=stream,
-                                                  schedule=sc)), max(10, steps // 3))
+    for rows in (32, 16, 64):
+        for pers in (0, 1):
+            for il in (0, 1):
+                sc = {"persistent": pers, "largest_first": 0, "interleave_rows": il,
+                      "tile_rows": rows}
+                by_schedule[f"tile_rows={rows},persistent={pers},interleave_rows={il}"] = timed(
+                    graph_of(lambda: sb.stylize_batch(batch, w.blend_radius, stream=stream,
+                                                      schedule=sc)), max(10, steps // 3))
     ms_single = timed(graph_of(singles), max(3, steps // 2)) / FRAMES_PER_STEP
     lut.destroy()
     peaks = measured_peaks()
@@ -878,11 +882,12 @@ def run_uneven(dev, n_frames: int = 64, n_exemplars: int = 8, seed: int = 4000,
     best, _ = sb.autotune_batch(frames, 2, reps=3)
     ms_tuned = timed(lambda: sb.stylize_batch(frames, 2, schedule=best))
     per_schedule = {}
-    for pers in (0, 1):
-        for lf in (0, 1):
-            sc = {"persistent": pers, "largest_first": lf}
-            per_schedule[f"persistent={pers},largest_first={lf}"] = timed(
-                lambda: sb.stylize_batch(frames, 2, schedule=sc))
+    for rows in (32, 16, 64):
+        for pers in (0, 1):
+            for lf in (0, 1):
+                sc = {"persistent": pers, "largest_first": lf, "tile_rows": rows}
+                per_schedule[f"tile_rows={rows},persistent={pers},largest_first={lf}"] = timed(
+                    lambda: sb.stylize_batch(frames, 2, schedule=sc))
     torch.cuda.synchronize()
     equal = all(torch.equal(f.out, o) for f, (_, _, _, _, _, o) in zip(frames, singles))
     for _, _, lut in exs:
@@ -1001,8 +1006,8 @@ def profile_once(args):
     lut = sb.build_lut(gs, ex.lut_bits)
     batch = [sb.BatchFrame(to_dev(f), lut, st, w.levels, w.threshold, w.seed + i)
              for i, f in enumerate(frames)]
-    pers, lf, il = (int(v) for v in args.schedule.split(","))
-    sched = {"persistent": pers, "largest_first": lf, "interleave_rows": il}
+    pers, lf, il, rows = (int(v) for v in args.schedule.split(","))
+    sched = {"persistent": pers, "largest_first": lf, "interleave_rows": il, "tile_rows": rows}
     for _ in range(2):
         sb.stylize_batch(batch, w.blend_radius, schedule=sched)
     # then the lookup-only comparator over the same frames, batched, twice

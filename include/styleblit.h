@@ -300,21 +300,27 @@ SB_API sb_status sb_stylize_batch(const sb_frame *frames, int32_t n_frames, int3
  *   largest_first  0: tiles in frame order; 1: frames with more tiles first
  *                  (shorter tail for uneven batches).
  *   interleave_rows  0: each frame's tiles together; 1: when every frame of
- *                  the batch has the same tile grid (64 x 32-pixel tiles),
+ *                  the batch has the same tile grid (in tiles of tile_rows),
  *                  tile row r of every frame before tile row r + 1, so the
  *                  exemplar lines those rows gather stay in L2 while the frames
  *                  stream through; batches of frames with different tile grids
  *                  keep frame order.
+ *   tile_rows      output rows per tile (tiles are 64 pixels wide): 0 or 32
+ *                  (256 threads a CTA), 16 (128 threads) or 64 (512 threads);
+ *                  16 and 64 need blend_radius <= 7.  Shorter tiles recompute
+ *                  a larger share of halo rows, taller ones use more shared
+ *                  memory per CTA.
  */
 typedef struct {
     int32_t persistent;
     int32_t largest_first;
     int32_t interleave_rows;
+    int32_t tile_rows;
 } sb_batch_schedule;
 
 /*
  * sb_stylize_batch_sched -- sb_stylize_batch with an explicit schedule
- * (NULL: {0, 0, 0}, the schedule of sb_stylize_batch).  Same arguments, outputs
+ * (NULL: {0, 0, 0, 0}, the schedule of sb_stylize_batch).  Same arguments, outputs
  * and errors as sb_stylize_batch.
  */
 SB_API sb_status sb_stylize_batch_sched(const sb_frame *frames, int32_t n_frames,
@@ -323,8 +329,9 @@ SB_API sb_status sb_stylize_batch_sched(const sb_frame *frames, int32_t n_frames
 
 /*
  * sb_autotune_batch -- picks the fastest schedule for this batch (no
- * counterpart in the paper).  Runs each schedule (persistent x largest_first,
- * times interleave_rows when the frames share one tile grid) once untimed and
+ * counterpart in the paper).  Runs each schedule (tile_rows 32, and 16 and 64
+ * for blend radii up to 7, times persistent x largest_first, times
+ * interleave_rows when the frames share one tile grid) once untimed and
  * `reps` times between two CUDA events on `stream`, waits for the stream, and
  * writes the fastest to *best and its mean time per batch (ms) to *best_ms
  * (nullable).  The batch's outputs are written (every run writes the same

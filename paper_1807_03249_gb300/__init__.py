@@ -64,7 +64,7 @@ class _Rgba8(ctypes.Structure):
 
 class _Schedule(ctypes.Structure):
     _fields_ = [("persistent", ctypes.c_int32), ("largest_first", ctypes.c_int32),
-                ("interleave_rows", ctypes.c_int32)]
+                ("interleave_rows", ctypes.c_int32), ("tile_rows", ctypes.c_int32)]
 
 
 class _Frame(ctypes.Structure):
@@ -335,8 +335,8 @@ def _frames_array(frames):
 def stylize_batch(frames, radius: int, stream=None, schedule: dict | None = None):
     """Stylises up to MAX_BATCH frames (BatchFrame) in one launch; returns their
     outputs.  Frames share the guide format and the blend radius.  `schedule`
-    ({"persistent": 0/1, "largest_first": 0/1, "interleave_rows": 0/1}, e.g.
-    from autotune_batch; missing keys are 0)
+    ({"persistent": 0/1, "largest_first": 0/1, "interleave_rows": 0/1,
+    "tile_rows": 0/16/32/64}, e.g. from autotune_batch; missing keys are 0)
     picks the launch form; every schedule gives the same pixels."""
     lib = load_library()
     frames = list(frames)
@@ -345,7 +345,7 @@ def stylize_batch(frames, radius: int, stream=None, schedule: dict | None = None
         _check("sb_stylize_batch", lib.sb_stylize_batch(arr, len(frames), radius, _stream(stream)))
     else:
         sc = _Schedule(int(schedule.get("persistent", 0)), int(schedule.get("largest_first", 0)),
-                       int(schedule.get("interleave_rows", 0)))
+                       int(schedule.get("interleave_rows", 0)), int(schedule.get("tile_rows", 0)))
         _check("sb_stylize_batch_sched",
                lib.sb_stylize_batch_sched(arr, len(frames), radius, ctypes.byref(sc),
                                           _stream(stream)))
@@ -374,7 +374,7 @@ def autotune_batch(frames, radius: int, reps: int = 5, stream=None):
                                                       ctypes.byref(best), ctypes.byref(ms),
                                                       _stream(stream)))
     return {"persistent": best.persistent, "largest_first": best.largest_first,
-            "interleave_rows": best.interleave_rows}, ms.value
+            "interleave_rows": best.interleave_rows, "tile_rows": best.tile_rows}, ms.value
 
 
 def stylize_batch_host(guides_host, luts, styles, levels, thresholds, seeds, radius: int,

@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             print(res.stdout + res.stderr, file=sys.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"]

@@ -50,9 +50,17 @@
 namespace sb {
 
 constexpr int kTW = 64;
-constexpr int kTH = 32;
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+constexpr int kTH = 32;        // default tile height (sb_stylize, sb_blend, sb_assign_chunks)
+
+// A tile of 64 x TH output pixels: 8 * TH threads, four output rows per warp.
+// Batches may use TH = 16, 32 or 64 (the autotuner's tile shapes).
+template <int TH>
+struct Tile {
+    static_assert(TH == 16 || TH == 32 || TH == 64, "tile height");
+    static constexpr int H = TH;
+    static constexpr int Threads = 8 * TH;
+    static constexpr int Warps = Threads / 32;
+};
 constexpr int kEagerMinLevel = 3;           // levels >= this get their cells in phase 0
 constexpr int kKeyShift = 11;               // cell-index bits of the packed seed key
 constexpr int kPackedMaxLevel = 8;          // levels whose packed keys fit 32 bits
@@ -99,10 +107,11 @@ struct SmemLayout {
 // Shared memory of one tile.  The vote's masks overlay the target guide of
 // the region, which is dead once the assignment is done; the level bytes exist
 // only for the assignment-only kernel (the fused path never stores levels).
-__host__ __device__ inline SmemLayout smem_layout(int r, int levels, bool level_bytes = false) {
+__host__ __device__ inline SmemLayout smem_layout(int r, int levels, bool level_bytes = false,
+                                                  int th = kTH) {
     SmemLayout s;
     s.RW = kTW + 2 * r;
-    s.RH = kTH + 2 * r;
+    s.RH = th + 2 * r;
     s.NR = s.RW * s.RH;
     s.NC = 0;
     for (int l = 1; l <= levels; ++l) s.NC += cells_bound(s.RW, s.RH, l);
@@ -128,11 +137,12 @@ __host__ __device__ inline SmemLayout smem_layout(int r, int levels, bool level_
     s.total = o;
     return s;
 }
-__host__ __device__ constexpr bool vote_masks_fit(int r) {
-    return (8 * 4 + 3 * 8) * (kTH + 2 * r) + 2 * 8 * kTH <= 4 * (kTW + 2 * r) * (kTH + 2 * r) &&
-           (r == 15 || vote_masks_fit(r + 1));
+__host__ __device__ constexpr bool vote_masks_fit(int r, int th) {
+    return (8 * 4 + 3 * 8) * (th + 2 * r) + 2 * 8 * th <= 4 * (kTW + 2 * r) * (th + 2 * r) &&
+           (r == 15 || vote_masks_fit(r + 1, th));
 }
-static_assert(vote_masks_fit(0), "the vote masks fit in the region guide's shared memory");
+static_assert(vote_masks_fit(0, 16) && vote_masks_fit(0, 32) && vote_masks_fit(0, 64),
+              "the vote masks fit in the region guide's shared memory");
 
 // Block-wide append to a shared list; every lane of the warp must call it.
 __device__ __forceinline__ void list_push(bool pred, int val, uint16_t *list, int *counter) {
@@ -248,16 +258,16 @@ __device__ __forceinline__ uint32_t seed_source(const FrameArgs &a, uint32_t g) 
                           bin_representative<C, B>(g, a.key_bits, a.key_channels), a.key_channels);
 }
 
-// Builds cells k0, k0 + kThreads, ... of the levels l_hi down to l_lo into
+// Builds cells k0, k0 + NT, ... (NT threads) of the levels l_hi down to l_lo into
 // cells[base_hi + k].
-template <int C, int B>
+template <int C, int B, int NT>
 __device__ __forceinline__ void build_cells(const FrameArgs &a, int4 *cells, int l_hi, int l_lo,
                                             int base_hi, int xa, int xb, int ya, int yb,
                                             int cxo, int cyo, int k0 = 0, int total = -1) {
     using F = GuideFmt<C, B>;
     if (total < 0) total = cell_count(l_hi, l_lo, xa, xb, ya, yb);
 #pragma unroll 1
-    for (int k = k0 + (int)threadIdx.x; k < total; k += kThreads) {
+    for (int k = k0 + (int)threadIdx.x; k < total; k += NT) {
         const CellTask t = cell_task(a, k, l_hi, xa, xb, ya, yb);
         const uint32_t u = seed_source<C, B>(a, F::load(a.tgt, a.tgt_stride, t.sx, t.sy));
         cells[base_hi + k] = cell_value(t, u, cxo, cyo);
@@ -268,11 +278,11 @@ __device__ __forceinline__ void build_cells(const FrameArgs &a, int4 *cells, int
 // 4 cover the region (the tile plus its R halo): segment s takes region column
 // s % RW, so the lanes of a warp hold neighbouring columns.  At every level
 // >= 2 a segment lies inside one seed cell.
-template <int R>
+template <int R, int TH>
 struct Segs {
     static constexpr int kPad = (R + 3) / 4 * 4;  // first segment row: kPad rows above the tile
-    static constexpr int RW = kTW + 2 * R, RH = kTH + 2 * R;
-    static constexpr int NSY = (kTH + 2 * kPad) / 4;
+    static constexpr int RW = kTW + 2 * R, RH = TH + 2 * R;
+    static constexpr int NSY = (TH + 2 * kPad) / 4;
     static constexpr int NS = RW * NSY;
     __device__ __forceinline__ static int rx(int s) { return s % RW; }
     __device__ __forceinline__ static int ry(int s) { return 4 * (s / RW) - kPad + R; }
@@ -288,15 +298,15 @@ struct Segs {
 // The region's columns [c_lo, c_hi) and rows [r_lo, r_hi) inside the target.
 struct TileBounds {
     int c_lo, c_hi, r_lo, r_hi;
-    template <int R>
+    template <int R, int TH>
     __device__ __forceinline__ static TileBounds of(int rx0, int ry0, int W, int H) {
         return TileBounds{max(0, -rx0), min(kTW + 2 * R, W - rx0), max(0, -ry0),
-                          min(kTH + 2 * R, H - ry0)};
+                          min(TH + 2 * R, H - ry0)};
     }
     // bit j: pixel (rx, ry + j) of a segment lies in the region and the target
-    template <int R>
+    template <int R, int TH>
     __device__ __forceinline__ uint32_t mask(int rx, int ry) const {
-        return rx >= c_lo && rx < c_hi ? Segs<R>::span(ry, r_lo, r_hi) : 0u;
+        return rx >= c_lo && rx < c_hi ? Segs<R, TH>::span(ry, r_lo, r_hi) : 0u;
     }
 };
 
@@ -351,14 +361,14 @@ __device__ __forceinline__ uint32_t test_segment(const SrcView &a, const uint32_
 // two cells) and the levels above kPackedMaxLevel (keys are 64-bit squared
 // distances packed with the cell index).  Both are rare, so pixels go one at
 // a time with little live state (the common path keeps its registers).
-template <int C, int B, int R>
+template <int C, int B, int R, int TH>
 __device__ __forceinline__ uint32_t segment_level_rare(const SrcView &a, const uint32_t *gt,
                                                        uint32_t *A, uint8_t *lev,
                                                        const int4 *cells, int base, int c0,
                                                        int ncy, int l, uint32_t t32, int rx,
                                                        int ry, uint32_t m) {
     using F = GuideFmt<C, B>;
-    constexpr int RW = Segs<R>::RW, RH = Segs<R>::RH;
+    constexpr int RW = Segs<R, TH>::RW, RH = Segs<R, TH>::RH;
     constexpr int kMask = (1 << kKeyShift) - 1;
     const int prx = rx - RW / 2, pry = ry - RH / 2;
     const bool packed = l <= kPackedMaxLevel;
@@ -417,13 +427,13 @@ __device__ __forceinline__ uint32_t segment_level_rare(const SrcView &a, const u
 // convex set: when the first and last pixel of m pick the same seed, every
 // pixel between them does and the nine-way search runs once.  Otherwise each
 // pixel searches (level 1 and the unscaled levels: segment_level_rare).
-template <int C, int B, int R>
+template <int C, int B, int R, int TH>
 __device__ __forceinline__ uint32_t segment_level(const FrameArgs &a, const uint32_t *gt,
                                                   uint32_t *A, uint8_t *lev, const int4 *cells,
                                                   int base, const LevelCells &g, int l, int rx0,
                                                   int ry0, uint32_t t32, int rx, int ry,
                                                   uint32_t m) {
-    using S = Segs<R>;
+    using S = Segs<R, TH>;
     constexpr int RW = S::RW, RH = S::RH;
     constexpr int kMask = (1 << kKeyShift) - 1;
     const int prx = rx - RW / 2, pry = ry - RH / 2;
@@ -431,7 +441,7 @@ __device__ __forceinline__ uint32_t segment_level(const FrameArgs &a, const uint
     const int ibase = ry * RW + rx;
     const SrcView sv{a.src_packed, a.Ws, a.Hs, a.threshold};
     if (l == 1 || l > kPackedMaxLevel)
-        return segment_level_rare<C, B, R>(sv, gt, A, lev, cells, base, c0, g.ncy, l, t32, rx, ry,
+        return segment_level_rare<C, B, R, TH>(sv, gt, A, lev, cells, base, c0, g.ncy, l, t32, rx, ry,
                                            m);
     // every lane evaluates the nine keys at all four pixels (three adds per
     // cell on top of the first pixel's key): no lane waits for a neighbour
@@ -464,23 +474,23 @@ __device__ __forceinline__ uint32_t segment_level(const FrameArgs &a, const uint
 // (its in-target pixels), lower levels the list of segments with pending
 // pixels (entries: segment index << 4 | pixel mask).  Segments with rejected
 // pixels are appended to list_out.
-template <int C, int B, int R>
+template <int C, int B, int R, int TH>
 __device__ __forceinline__ void level_segments(const FrameArgs &a, const uint32_t *gt,
                                                uint32_t *A, uint8_t *lev, const int4 *cells,
                                                int base, const LevelCells &g, int l, int rx0,
                                                int ry0, const TileBounds &tb, uint32_t t32,
                                                bool top, const uint16_t *list_in, int n_in,
                                                uint16_t *list_out, int *cnt_out) {
-    using S = Segs<R>;
+    using S = Segs<R, TH>;
     const int n = top ? S::NS : n_in;
-    for (int s0 = 0; s0 < n; s0 += kThreads) {
+    for (int s0 = 0; s0 < n; s0 += Tile<TH>::Threads) {
         const int jj = s0 + (int)threadIdx.x;
         int sg = 0;
         uint32_t m = 0;
         if (jj < n) {
             if (top) {
                 sg = jj;
-                m = tb.template mask<R>(S::rx(sg), S::ry(sg));
+                m = tb.template mask<R, TH>(S::rx(sg), S::ry(sg));
             } else {
                 const uint32_t e = list_in[jj];
                 sg = (int)(e >> 4);
@@ -489,7 +499,7 @@ __device__ __forceinline__ void level_segments(const FrameArgs &a, const uint32_
         }
         uint32_t rej = 0;
         if (m)
-            rej = segment_level<C, B, R>(a, gt, A, lev, cells, base, g, l, rx0, ry0, t32,
+            rej = segment_level<C, B, R, TH>(a, gt, A, lev, cells, base, g, l, rx0, ry0, t32,
                                          S::rx(sg), S::ry(sg), m);
         list_push(rej != 0, (sg << 4) | (int)rej, list_out, cnt_out);
     }
@@ -498,11 +508,12 @@ __device__ __forceinline__ void level_segments(const FrameArgs &a, const uint32_
 // ---------------------------------------------------------------------------
 // assignment of the region held in shared memory (Algorithm 2)
 // ---------------------------------------------------------------------------
-template <int C, int B, int R>
+template <int C, int B, int R, int TH>
 __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayout &L, int rx0,
                                               int ry0, unsigned char *smem, uint8_t *lev) {
     using F = GuideFmt<C, B>;
-    constexpr int RW = kTW + 2 * R, RH = kTH + 2 * R;
+    constexpr int RW = kTW + 2 * R, RH = TH + 2 * R;
+    constexpr int kThreads = Tile<TH>::Threads;
     int4 *cells = reinterpret_cast<int4 *>(smem + L.off_cells);
     uint32_t *gt = reinterpret_cast<uint32_t *>(smem + L.off_gt);
     uint32_t *A = reinterpret_cast<uint32_t *>(smem + L.off_A);
@@ -517,7 +528,7 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     const uint32_t t32 = a.threshold > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)a.threshold;
     const int L_top = a.levels;
     const int eager_lo = L_top <= kEagerMinLevel ? 1 : kEagerMinLevel;
-    const TileBounds tb = TileBounds::of<R>(rx0, ry0, a.W, a.H);
+    const TileBounds tb = TileBounds::of<R, TH>(rx0, ry0, a.W, a.H);
 
     if (tid == 0) {
         cnt[0] = 0;
@@ -582,26 +593,27 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     }
     if (has_cell) cells[tid] = cell_value(ct, cu, cxo, cyo);
     if (n_eager > kThreads)
-        build_cells<C, B>(a, cells, L_top, eager_lo, 0, xa, xb, ya, yb, cxo, cyo, kThreads, n_eager);
+        build_cells<C, B, kThreads>(a, cells, L_top, eager_lo, 0, xa, xb, ya, yb, cxo, cyo, kThreads,
+                                    n_eager);
     __syncthreads();
 
     // level step t (0 = top) appends to counter t % 3; the counter of step
     // t + 1 is cleared during step t (its last reader passed step t - 1's
     // barrier), so one barrier per level publishes both the list and the reset.
     // The top level visits every segment of the region; its cells start at 0.
-    int n_pend = Segs<R>::NS, base = 0;
+    int n_pend = Segs<R, TH>::NS, base = 0;
     const uint16_t *list_cur = list0;
     uint16_t *list_nxt = list1;
     for (int l = L_top, t = 0; l >= 1 && n_pend > 0; --l, ++t) {
         const LevelCells g = level_cells(l, xa, xb, ya, yb);
         if (l == kEagerMinLevel - 1 && eager_lo > 1) {
             // a pixel still needs the fine levels: build levels 2 and 1 now
-            build_cells<C, B>(a, cells, l, 1, base, xa, xb, ya, yb, cxo, cyo);
+            build_cells<C, B, kThreads>(a, cells, l, 1, base, xa, xb, ya, yb, cxo, cyo);
             __syncthreads();
         }
         if (tid == 0) cnt[(t + 1) % 3] = 0;
-        level_segments<C, B, R>(a, gt, A, lev, cells, base, g, l, rx0, ry0, tb, t32, t == 0,
-                                list_cur, n_pend, list_nxt, &cnt[t % 3]);
+        level_segments<C, B, R, TH>(a, gt, A, lev, cells, base, g, l, rx0, ry0, tb, t32, t == 0,
+                                    list_cur, n_pend, list_nxt, &cnt[t % 3]);
         __syncthreads();
         n_pend = cnt[t % 3];
         base += g.ncx * g.ncy;
@@ -739,17 +751,19 @@ __device__ __forceinline__ uint32_t window_steps(const uint32_t *E, int ry, int 
 
 // Windows whose rows have at most two runs each: one gather per run (the
 // second has length 0 in a single-run row).
-template <int R, bool F32>
+template <int R, bool F32, int NT>
 __device__ __forceinline__ void vote_two_runs(const FrameArgs &a, const StyleView &sv,
                                               const uint32_t *A, const uint32_t *E,
                                               const uint16_t *list, int n, int x0, int y0) {
     constexpr int RW = kTW + 2 * R;
     constexpr bool kPacked = (2 * R + 1) * (2 * R + 1) * 255 < 65536;
-    for (int j = threadIdx.x; j < n; j += kThreads) {
+    for (int j = threadIdx.x; j < n; j += NT) {
         const int k = list[j];
         const int tx = k % kTW, ty = k / kTW;
         VoteAcc<kPacked> acc;
-#pragma unroll
+        // windows above 15 x 15 (one CTA per SM, rarely used) stay rolled
+        constexpr int kUnroll = R <= 7 ? 2 * R + 1 : 1;
+#pragma unroll kUnroll
         for (int oy = -R; oy <= R; ++oy) {
             const int ry = ty + R + oy;
             const uint32_t *row = A + ry * RW;
@@ -764,19 +778,20 @@ __device__ __forceinline__ void vote_two_runs(const FrameArgs &a, const StyleVie
 
 // Every other window (junctions of three or more chunks, frame borders): tap
 // by tap.  The block's such pixels share one list.
-template <int R, bool F32>
+template <int R, bool F32, int NT>
 __device__ __forceinline__ void vote_taps(const FrameArgs &a, const StyleView &sv,
                                           const uint32_t *A, const uint16_t *list, int n, int x0,
                                           int y0) {
     constexpr int RW = kTW + 2 * R;
     constexpr bool kPacked = (2 * R + 1) * (2 * R + 1) * 255 < 65536;
-    for (int j = threadIdx.x; j < n; j += kThreads) {
+    for (int j = threadIdx.x; j < n; j += NT) {
         const int k = list[j];
         const int tx = k % kTW, ty = k / kTW;
         VoteAcc<kPacked> acc;
         for (int oy = -R; oy <= R; ++oy) {
             const uint32_t *row = A + (ty + R + oy) * RW + tx + R;
-#pragma unroll
+            constexpr int kUnroll = R <= 7 ? 2 * R + 1 : 1;
+#pragma unroll kUnroll
             for (int ox = -R; ox <= R; ++ox) sv.add(acc, tap_pos(row[ox], ox, oy), 1u);
         }
         vote_store<F32, R>(a, acc, x0 + tx, y0 + ty);
@@ -791,9 +806,9 @@ __device__ __forceinline__ uint64_t shr128(uint64_t lo, uint64_t hi, int j) {
 // Shared-memory words of the vote's masks: per region row E (4 words), V (4
 // words) and the 64-bit output-column masks hu, t2, vc; per output row the
 // 64-bit class masks U and T2.
-template <int R>
+template <int R, int TH>
 struct VoteMasks {
-    static constexpr int RH = kTH + 2 * R;
+    static constexpr int RH = TH + 2 * R;
     uint32_t *E, *V;
     uint64_t *hu, *t2, *vc, *U, *T2;
     __device__ __forceinline__ static VoteMasks at(unsigned char *p) {
@@ -804,18 +819,19 @@ struct VoteMasks {
         m.t2 = m.hu + RH;
         m.vc = m.t2 + RH;
         m.U = m.vc + RH;
-        m.T2 = m.U + kTH;
+        m.T2 = m.U + TH;
         return m;
     }
 };
 
-template <int R, bool F32>
+template <int R, bool F32, int TH>
 __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &L, int x0,
                                           int y0, const uint32_t *A, unsigned char *smem) {
-    constexpr int RW = kTW + 2 * R, RH = kTH + 2 * R;
+    constexpr int RW = kTW + 2 * R, RH = TH + 2 * R;
+    constexpr int kThreads = Tile<TH>::Threads, kWarps = Tile<TH>::Warps;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const StyleView sv = StyleView::of(a);
-    const VoteMasks<R> mk = VoteMasks<R>::at(smem + L.off_masks);
+    const VoteMasks<R, TH> mk = VoteMasks<R, TH>::at(smem + L.off_masks);
     if (R > 0 && threadIdx.x == 0) {
         int *cnt = reinterpret_cast<int *>(smem + L.off_cnt);
         cnt[3] = cnt[4] = 0;  // two-runs and tap-by-tap list lengths
@@ -853,7 +869,8 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
             const uint32_t *e = mk.E + 4 * ry, *v = mk.V + 4 * ry;
             const uint64_t blo = ~((uint64_t)e[0] | ((uint64_t)e[1] << 32)), bhi = ~(uint64_t)e[2];
             uint64_t seen = 0, two = 0;
-#pragma unroll
+            constexpr int kUnroll = R <= 7 ? 2 * R : 1;
+#pragma unroll kUnroll
             for (int s = 1; s <= 2 * R; ++s) {
                 const uint64_t b = shr128(blo, bhi, s);
                 two |= seen & b;
@@ -866,7 +883,7 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
         __syncthreads();
         // one thread per output row: uniform windows (one translation) and
         // windows whose rows have at most two runs
-        if (threadIdx.x < kTH) {
+        if (threadIdx.x < TH) {
             const int ty = threadIdx.x;
             uint64_t U = mk.hu[ty], T2 = mk.t2[ty];
 #pragma unroll
@@ -883,7 +900,7 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
     // exactly C_S[A(p)] (all its taps share one source position; outside the
     // source the vote is 0); the other pixels go to two block-wide lists, their
     // membership read off warp-uniform 64-bit row masks.
-    constexpr int kRowsPerWarp = kTH / kWarps;
+    constexpr int kRowsPerWarp = TH / kWarps;
     const int wcols = min(a.W - x0, kTW);  // columns of the tile inside the target
     const uint64_t incols = wcols >= 64 ? ~0ull : ((1ull << wcols) - 1ull);
     uint32_t col[kRowsPerWarp][2];
@@ -961,22 +978,22 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
             }
         }
         __syncthreads();
-        vote_two_runs<R, F32>(a, sv, A, mk.E, glist, cnt[3], x0, y0);
-        vote_taps<R, F32>(a, sv, A, tlist, cnt[4], x0, y0);
+        vote_two_runs<R, F32, kThreads>(a, sv, A, mk.E, glist, cnt[3], x0, y0);
+        vote_taps<R, F32, kThreads>(a, sv, A, tlist, cnt[4], x0, y0);
     }
 }
 
-// One 64 x 32 output tile (tile_x, tile_y) of one frame.
-template <int C, int B, int MODE, int R>
+// One 64 x TH output tile (tile_x, tile_y) of one frame.
+template <int C, int B, int MODE, int R, int TH = kTH>
 __device__ __forceinline__ void frame_tile(const FrameArgs &a, const SmemLayout &L, int tile_x,
                                            int tile_y, unsigned char *smem) {
-    const int x0 = tile_x * kTW, y0 = tile_y * kTH;
+    const int x0 = tile_x * kTW, y0 = tile_y * TH;
     uint8_t *bytes = smem + L.off_bytes;
-    assign_region<C, B, R>(a, L, x0 - R, y0 - R, smem, MODE == kAssign ? bytes : nullptr);
+    assign_region<C, B, R, TH>(a, L, x0 - R, y0 - R, smem, MODE == kAssign ? bytes : nullptr);
     const uint32_t *A = reinterpret_cast<const uint32_t *>(smem + L.off_A);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if constexpr (MODE == kAssign) {
-        for (int ty = warp; ty < kTH; ty += kWarps) {
+        for (int ty = warp; ty < TH; ty += Tile<TH>::Warps) {
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const int tx = c * 32 + lane;
@@ -988,18 +1005,20 @@ __device__ __forceinline__ void frame_tile(const FrameArgs &a, const SmemLayout 
             }
         }
     } else {
-        vote_tile<R, false>(a, L, x0, y0, A, smem);
+        vote_tile<R, false, TH>(a, L, x0, y0, A, smem);
     }
 }
 
 // CTAs per SM the kernels are compiled for: four (64 registers a thread) hide
 // more of each tile's load latency than three with 80 registers; five (48)
 // spill too much.  Windows above 15 x 15 need more than a quarter of the
-// SM's shared memory anyway, so they are compiled for one CTA per SM.
-__host__ __device__ constexpr int min_ctas(int r) { return r <= 7 ? 4 : 1; }
+// SM's shared memory anyway, so they are compiled for one CTA per SM.  Other
+// tile heights keep 64 registers a thread: 8, 4 or 2 CTAs of 128, 256 or 512
+// threads.
+__host__ __device__ constexpr int min_ctas(int r, int th = kTH) { return r <= 7 ? 128 / th : 1; }
 
 template <int C, int B, int MODE, int R>
-__global__ void __launch_bounds__(kThreads, min_ctas(R))
+__global__ void __launch_bounds__(Tile<kTH>::Threads, min_ctas(R))
     frame_kernel(const FrameArgs a, const SmemLayout L) {
     extern __shared__ __align__(16) unsigned char smem[];
     frame_tile<C, B, MODE, R>(a, L, blockIdx.x, blockIdx.y, smem);
@@ -1027,7 +1046,7 @@ struct BatchArgs {
 // Tile t of a batch: the frame k with tile_start[k] <= t < tile_start[k + 1]
 // (frame by frame), or tile row t / (n * rows_tx) of frame (t / rows_tx) % n
 // (rows interleaved).
-template <int C, int B, int R>
+template <int C, int B, int R, int TH>
 __device__ __forceinline__ void batch_tile(const BatchArgs &b, const SmemLayout &L, int t,
                                            unsigned char *smem) {
     if (b.rows_interleaved) {
@@ -1035,7 +1054,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &b, const SmemLayout 
         const int r = t / per_row, rem = t - r * per_row;
         const int k = rem / b.rows_tx;
         const FrameArgs a = b.f[k];
-        frame_tile<C, B, kStylize, R>(a, L, rem - k * b.rows_tx, r, smem);
+        frame_tile<C, B, kStylize, R, TH>(a, L, rem - k * b.rows_tx, r, smem);
         return;
     }
     int lo = 0, hi = b.n - 1;  // last frame whose first tile is <= t
@@ -1046,14 +1065,14 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &b, const SmemLayout 
     }
     const FrameArgs a = b.f[lo];  // register copy: field reads become plain operands
     const int lt = t - b.tile_start[lo];
-    frame_tile<C, B, kStylize, R>(a, L, lt % b.tiles_x[lo], lt / b.tiles_x[lo], smem);
+    frame_tile<C, B, kStylize, R, TH>(a, L, lt % b.tiles_x[lo], lt / b.tiles_x[lo], smem);
 }
 
-template <int C, int B, int R>
-__global__ void __launch_bounds__(kThreads, min_ctas(R))
+template <int C, int B, int R, int TH>
+__global__ void __launch_bounds__(Tile<TH>::Threads, min_ctas(R, TH))
     batch_kernel(const __grid_constant__ BatchArgs b, const SmemLayout L) {
     extern __shared__ __align__(16) unsigned char smem[];
-    batch_tile<C, B, R>(b, L, (int)blockIdx.x, smem);
+    batch_tile<C, B, R, TH>(b, L, (int)blockIdx.x, smem);
 }
 
 // Work queue of a persistent batch launch: CTAs take the next tile from
@@ -1065,8 +1084,8 @@ struct TileQueue {
     unsigned int next, done;
 };
 
-template <int C, int B, int R>
-__global__ void __launch_bounds__(kThreads, min_ctas(R))
+template <int C, int B, int R, int TH>
+__global__ void __launch_bounds__(Tile<TH>::Threads, min_ctas(R, TH))
     batch_kernel_persistent(const __grid_constant__ BatchArgs b, const SmemLayout L,
                             TileQueue *q) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1078,7 +1097,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas(R))
         const int t = tile;
         __syncthreads();  // every thread has read `tile` before it is overwritten
         if (t >= n_tiles) break;
-        batch_tile<C, B, R>(b, L, t, smem);
+        batch_tile<C, B, R, TH>(b, L, t, smem);
         __syncthreads();  // the tile's shared memory is free before the next tile writes it
     }
     if (threadIdx.x == 0) {
@@ -1091,7 +1110,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas(R))
 }
 
 template <bool F32, int R>
-__global__ void __launch_bounds__(kThreads) blend_kernel(const FrameArgs a) {
+__global__ void __launch_bounds__(Tile<kTH>::Threads) blend_kernel(const FrameArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int RW = kTW + 2 * R, NR = RW * (kTH + 2 * R);
     const SmemLayout L = smem_layout(R, 0);
@@ -1099,13 +1118,13 @@ __global__ void __launch_bounds__(kThreads) blend_kernel(const FrameArgs a) {
     const int rx0 = x0 - R, ry0 = y0 - R;
     uint32_t *A = reinterpret_cast<uint32_t *>(smem + L.off_A);
 #pragma unroll 4
-    for (int i = threadIdx.x; i < NR; i += kThreads) {
+    for (int i = threadIdx.x; i < NR; i += Tile<kTH>::Threads) {
         const int gx = rx0 + i % RW, gy = ry0 + i / RW;
         const bool inside = gx >= 0 && gy >= 0 && gx < a.W && gy < a.H;
         A[i] = inside ? __ldg(a.assign_in + (int64_t)gy * a.W + gx) : kInvalid;
     }
     __syncthreads();
-    vote_tile<R, F32>(a, L, x0, y0, A, smem);
+    vote_tile<R, F32, kTH>(a, L, x0, y0, A, smem);
 }
 
 // Raises a kernel's dynamic shared-memory limit once per (kernel, device);
@@ -1134,7 +1153,7 @@ cudaError_t launch_tiles(size_t smem, int W, int H, cudaStream_t s, const Args &
     cudaError_t e = ensure_smem<Kernel>(smem);
     if (e != cudaSuccess) return e;
     dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH);
-    Kernel<<<grid, kThreads, smem, s>>>(args...);
+    Kernel<<<grid, Tile<kTH>::Threads, smem, s>>>(args...);
     return cudaGetLastError();
 }
 
@@ -1147,7 +1166,7 @@ cudaError_t launch_stylize_r(const FrameArgs &a, cudaStream_t s) {
 // CTAs of a persistent launch: as many as fit on the device at once (cached
 // per kernel, device and shared-memory size), at most one per tile.
 template <auto Kernel>
-int persistent_grid(size_t smem, int n_tiles) {
+int persistent_grid(size_t smem, int threads, int n_tiles) {
     constexpr int kMaxDev = 64;
     static std::atomic<uint64_t> cache[kMaxDev] = {};  // smem << 32 | CTAs
     int dev = 0;
@@ -1159,77 +1178,134 @@ int persistent_grid(size_t smem, int n_tiles) {
     } else {
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, Kernel, kThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, Kernel, threads, smem);
         ctas = max(1, sms * max(per_sm, 1));
         if (dev < kMaxDev) cache[dev].store(((uint64_t)smem << 32) | (uint32_t)ctas);
     }
     return min(ctas, n_tiles);
 }
 
-template <int C, int B, int R>
-cudaError_t launch_batch_r(const BatchArgs &b, int max_levels, TileQueue *queue, cudaStream_t s) {
+template <int C, int B, int R, int TH>
+cudaError_t launch_batch_rt(const BatchArgs &b, int max_levels, TileQueue *queue, cudaStream_t s) {
     // one layout (for the deepest frame) serves every tile of the launch
-    const SmemLayout L = smem_layout(R, max_levels);
+    constexpr int kThreads = Tile<TH>::Threads;
+    const SmemLayout L = smem_layout(R, max_levels, false, TH);
     const int n_tiles = b.tile_start[b.n];
     if (!queue) {
-        cudaError_t e = ensure_smem<batch_kernel<C, B, R>>(L.total);
+        cudaError_t e = ensure_smem<batch_kernel<C, B, R, TH>>(L.total);
         if (e != cudaSuccess) return e;
-        batch_kernel<C, B, R><<<n_tiles, kThreads, L.total, s>>>(b, L);
+        batch_kernel<C, B, R, TH><<<n_tiles, kThreads, L.total, s>>>(b, L);
         return cudaGetLastError();
     }
-    cudaError_t e = ensure_smem<batch_kernel_persistent<C, B, R>>(L.total);
+    cudaError_t e = ensure_smem<batch_kernel_persistent<C, B, R, TH>>(L.total);
     if (e != cudaSuccess) return e;
-    const int grid = persistent_grid<batch_kernel_persistent<C, B, R>>(L.total, n_tiles);
-    batch_kernel_persistent<C, B, R><<<grid, kThreads, L.total, s>>>(b, L, queue);
+    const int grid =
+        persistent_grid<batch_kernel_persistent<C, B, R, TH>>(L.total, kThreads, n_tiles);
+    batch_kernel_persistent<C, B, R, TH><<<grid, kThreads, L.total, s>>>(b, L, queue);
     return cudaGetLastError();
 }
 
-// Launches the batch kernel of guide format <C, B> for blend radius r: one CTA
-// per tile (queue == nullptr) or persistent CTAs over the given work queue.
-template <int C, int B, int R = 0>
-cudaError_t launch_batch(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
-                         cudaStream_t s) {
-    if (r == R) return launch_batch_r<C, B, R>(b, max_levels, queue, s);
-    if constexpr (R < kMaxFusedRadius) return launch_batch<C, B, R + 1>(b, r, max_levels, queue, s);
+// Blend radii with tiles of 16 and 64 rows besides the default 32, and the
+// largest radius of the first of the two radius ranges each format compiles in
+// separate translation units (they compile in parallel).
+constexpr int kMaxShapedRadius = 7;
+constexpr int kNarrowMaxRadius = 7;
+
+// Launches the batch kernel of guide format <C, B> for blend radius r in
+// [R, RMax] with tiles of 32 rows (launch_batch32) or of th = 16 or 64 rows (r
+// <= kMaxShapedRadius, launch_batch_shaped): one CTA per tile (queue ==
+// nullptr) or persistent CTAs over the given work queue.
+template <int C, int B, int R, int RMax>
+cudaError_t launch_batch32(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
+                           cudaStream_t s) {
+    if (r == R) return launch_batch_rt<C, B, R, 32>(b, max_levels, queue, s);
+    if constexpr (R < RMax) return launch_batch32<C, B, R + 1, RMax>(b, r, max_levels, queue, s);
     return cudaErrorInvalidValue;
 }
 
 template <int C, int B, int R = 0>
+cudaError_t launch_batch_shaped(const BatchArgs &b, int r, int th, int max_levels,
+                                TileQueue *queue, cudaStream_t s) {
+    if (r == R) {
+        if (th == 16) return launch_batch_rt<C, B, R, 16>(b, max_levels, queue, s);
+        if (th == 64) return launch_batch_rt<C, B, R, 64>(b, max_levels, queue, s);
+        return cudaErrorInvalidValue;
+    }
+    if constexpr (R < kMaxShapedRadius)
+        return launch_batch_shaped<C, B, R + 1>(b, r, th, max_levels, queue, s);
+    return cudaErrorInvalidValue;
+}
+
+// The fused frame kernel for blend radius a.radius in [R, RMax].
+template <int C, int B, int R, int RMax>
 cudaError_t launch_stylize(const FrameArgs &a, cudaStream_t s) {
     if (a.radius == R) return launch_stylize_r<C, B, R>(a, s);
-    if constexpr (R < kMaxFusedRadius) return launch_stylize<C, B, R + 1>(a, s);
+    if constexpr (R < RMax) return launch_stylize<C, B, R + 1, RMax>(a, s);
     return cudaErrorInvalidValue;
 }
 
-// Launches the frame kernel of guide format <C, B> in the given mode.
+// Launches the frame kernel of guide format <C, B> in the given mode (the
+// fused kernel for radii up to kNarrowMaxRadius; the wider ones through
+// launch_frame_wide_c<C>b<B>).
 template <int C, int B>
-cudaError_t launch_frame(int mode, const FrameArgs &a, cudaStream_t s) {
+cudaError_t launch_frame_narrow(int mode, const FrameArgs &a, cudaStream_t s) {
     if (mode == kAssign) {
         const SmemLayout L = smem_layout(0, a.levels, true);
         return launch_tiles<frame_kernel<C, B, kAssign, 0>>(L.total, a.W, a.H, s, a, L);
     }
-    return launch_stylize<C, B>(a, s);
+    return launch_stylize<C, B, 0, kNarrowMaxRadius>(a, s);
 }
 
-// per-format launchers, one translation unit each (sb_frame_c<C>b<B>.cu)
-// per-format batch launchers, defined next to the frame launchers
-cudaError_t launch_batch_c1b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
-                              cudaStream_t s);
-cudaError_t launch_batch_c2b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
-                              cudaStream_t s);
-cudaError_t launch_batch_c3b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
-                              cudaStream_t s);
-cudaError_t launch_batch_c4b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
-                              cudaStream_t s);
-cudaError_t launch_batch_c1b16(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
-                              cudaStream_t s);
-cudaError_t launch_batch_c2b16(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
-                              cudaStream_t s);
+// per-format launchers: frame kernels and 32-row batches of radii up to 7 in
+// sb_frame_c<C>b<B>.cu, radii 8-15 in sb_frame_c<C>b<B>_wide.cu, 16- and 64-row
+// batches in sb_frame_c<C>b<B>_shapes.cu
 cudaError_t launch_frame_c1b8(int mode, const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_frame_wide_c1b8(const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_batch_c1b8(const BatchArgs &b, int r, int th, int max_levels,
+                              TileQueue *queue, cudaStream_t s);
+cudaError_t launch_batch_wide_c1b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
+                                   cudaStream_t s);
+cudaError_t launch_batch_shaped_c1b8(const BatchArgs &b, int r, int th, int max_levels,
+                                     TileQueue *queue, cudaStream_t s);
 cudaError_t launch_frame_c2b8(int mode, const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_frame_wide_c2b8(const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_batch_c2b8(const BatchArgs &b, int r, int th, int max_levels,
+                              TileQueue *queue, cudaStream_t s);
+cudaError_t launch_batch_wide_c2b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
+                                   cudaStream_t s);
+cudaError_t launch_batch_shaped_c2b8(const BatchArgs &b, int r, int th, int max_levels,
+                                     TileQueue *queue, cudaStream_t s);
 cudaError_t launch_frame_c3b8(int mode, const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_frame_wide_c3b8(const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_batch_c3b8(const BatchArgs &b, int r, int th, int max_levels,
+                              TileQueue *queue, cudaStream_t s);
+cudaError_t launch_batch_wide_c3b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
+                                   cudaStream_t s);
+cudaError_t launch_batch_shaped_c3b8(const BatchArgs &b, int r, int th, int max_levels,
+                                     TileQueue *queue, cudaStream_t s);
 cudaError_t launch_frame_c4b8(int mode, const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_frame_wide_c4b8(const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_batch_c4b8(const BatchArgs &b, int r, int th, int max_levels,
+                              TileQueue *queue, cudaStream_t s);
+cudaError_t launch_batch_wide_c4b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
+                                   cudaStream_t s);
+cudaError_t launch_batch_shaped_c4b8(const BatchArgs &b, int r, int th, int max_levels,
+                                     TileQueue *queue, cudaStream_t s);
 cudaError_t launch_frame_c1b16(int mode, const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_frame_wide_c1b16(const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_batch_c1b16(const BatchArgs &b, int r, int th, int max_levels,
+                              TileQueue *queue, cudaStream_t s);
+cudaError_t launch_batch_wide_c1b16(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
+                                   cudaStream_t s);
+cudaError_t launch_batch_shaped_c1b16(const BatchArgs &b, int r, int th, int max_levels,
+                                     TileQueue *queue, cudaStream_t s);
 cudaError_t launch_frame_c2b16(int mode, const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_frame_wide_c2b16(const FrameArgs &a, cudaStream_t s);
+cudaError_t launch_batch_c2b16(const BatchArgs &b, int r, int th, int max_levels,
+                              TileQueue *queue, cudaStream_t s);
+cudaError_t launch_batch_wide_c2b16(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
+                                   cudaStream_t s);
+cudaError_t launch_batch_shaped_c2b16(const BatchArgs &b, int r, int th, int max_levels,
+                                     TileQueue *queue, cudaStream_t s);
 
 }  // namespace sb

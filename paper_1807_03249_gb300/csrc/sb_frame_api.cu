@@ -30,19 +30,19 @@ static cudaError_t launch_frame_any(int channels, int bits, int mode, const Fram
     return cudaErrorInvalidValue;
 }
 
-static cudaError_t launch_batch_any(int channels, int bits, const BatchArgs &b, int r,
+static cudaError_t launch_batch_any(int channels, int bits, const BatchArgs &b, int r, int th,
                                     TileQueue *queue, int max_levels, cudaStream_t s) {
     if (bits == 8) {
         switch (channels) {
-            case 1: return launch_batch_c1b8(b, r, max_levels, queue, s);
-            case 2: return launch_batch_c2b8(b, r, max_levels, queue, s);
-            case 3: return launch_batch_c3b8(b, r, max_levels, queue, s);
-            case 4: return launch_batch_c4b8(b, r, max_levels, queue, s);
+            case 1: return launch_batch_c1b8(b, r, th, max_levels, queue, s);
+            case 2: return launch_batch_c2b8(b, r, th, max_levels, queue, s);
+            case 3: return launch_batch_c3b8(b, r, th, max_levels, queue, s);
+            case 4: return launch_batch_c4b8(b, r, th, max_levels, queue, s);
         }
     } else if (bits == 16) {
         switch (channels) {
-            case 1: return launch_batch_c1b16(b, r, max_levels, queue, s);
-            case 2: return launch_batch_c2b16(b, r, max_levels, queue, s);
+            case 1: return launch_batch_c1b16(b, r, th, max_levels, queue, s);
+            case 2: return launch_batch_c2b16(b, r, th, max_levels, queue, s);
         }
     }
     return cudaErrorInvalidValue;
@@ -272,7 +272,7 @@ extern "C" sb_status sb_blend(const uint32_t *assign, int32_t tgt_w, int32_t tgt
 // order or, with largest_first, by decreasing tile count (each frame keeps its
 // own output, so the order changes only which tiles are issued first).
 static sb_status prepare_batch(const sb_frame *frames, int32_t n_frames, int32_t blend_radius,
-                               bool largest_first, bool interleave_rows, BatchArgs &b,
+                               bool largest_first, bool interleave_rows, int th, BatchArgs &b,
                                int &max_levels, int &channels, int &bits) {
     if (n_frames < 0 || n_frames > kMaxBatch)
         return fail(SB_ERR_INVALID_ARG, "n_frames must be in [0, 128]");
@@ -311,7 +311,7 @@ static sb_status prepare_batch(const sb_frame *frames, int32_t n_frames, int32_t
         const int64_t npx = (int64_t)f.tgt_guide.width * f.tgt_guide.height;
         if (npx > 0 && (!f.rgba8_out || ((uintptr_t)f.rgba8_out % 4)))
             return fail(SB_ERR_INVALID_ARG, std::string(name) + ": rgba8_out NULL or misaligned");
-        const int64_t tx = (f.tgt_guide.width + kTW - 1) / kTW, ty = (f.tgt_guide.height + kTH - 1) / kTH;
+        const int64_t tx = (f.tgt_guide.width + kTW - 1) / kTW, ty = (f.tgt_guide.height + th - 1) / th;
         tiles[k] = npx > 0 ? tx * ty : 0;
         order[k] = k;
         max_levels = max(max_levels, (int)f.levels);
@@ -334,11 +334,11 @@ static sb_status prepare_batch(const sb_frame *frames, int32_t n_frames, int32_t
     // rows interleaved only when every frame has the same tile grid
     if (interleave_rows) {
         const int tx0 = (frames[0].tgt_guide.width + kTW - 1) / kTW;
-        const int ty0 = (frames[0].tgt_guide.height + kTH - 1) / kTH;
+        const int ty0 = (frames[0].tgt_guide.height + th - 1) / th;
         bool same = tiles[0] > 0;
         for (int k = 1; k < n_frames && same; ++k)
             same = (frames[k].tgt_guide.width + kTW - 1) / kTW == tx0 &&
-                   (frames[k].tgt_guide.height + kTH - 1) / kTH == ty0 && tiles[k] > 0;
+                   (frames[k].tgt_guide.height + th - 1) / th == ty0 && tiles[k] > 0;
         if (same) {
             b.rows_interleaved = 1;
             b.rows_tx = tx0;
@@ -355,11 +355,16 @@ extern "C" sb_status sb_stylize_batch_sched(const sb_frame *frames, int32_t n_fr
                                             int32_t blend_radius,
                                             const sb_batch_schedule *schedule,
                                             sb_stream stream) {
-    const sb_batch_schedule sched = schedule ? *schedule : sb_batch_schedule{0, 0, 0};
-    static thread_local BatchArgs b;  // ~18 KB: kept off the stack
+    const sb_batch_schedule sched = schedule ? *schedule : sb_batch_schedule{0, 0, 0, 0};
+    const int th = sched.tile_rows == 0 ? kTH : sched.tile_rows;
+    if (th != 16 && th != 32 && th != 64)
+        return fail(SB_ERR_INVALID_ARG, "schedule.tile_rows must be 0, 16, 32 or 64");
+    if (th != kTH && blend_radius > kMaxShapedRadius)
+        return fail(SB_ERR_INVALID_ARG, "tiles of 16 or 64 rows need blend_radius <= 7");
+    static thread_local BatchArgs b;  // ~19 KB: kept off the stack
     int max_levels = 1, channels = 0, bits = 0;
     sb_status st = prepare_batch(frames, n_frames, blend_radius, sched.largest_first != 0,
-                                 sched.interleave_rows != 0, b, max_levels, channels, bits);
+                                 sched.interleave_rows != 0, th, b, max_levels, channels, bits);
     if (st != SB_OK || n_frames == 0 || b.tile_start[n_frames] == 0) return st;
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) return cuda_fail(e, "pending CUDA error");
@@ -367,7 +372,7 @@ extern "C" sb_status sb_stylize_batch_sched(const sb_frame *frames, int32_t n_fr
     if (sched.persistent &&
         (st = acquire_queue(static_cast<cudaStream_t>(stream), &queue)) != SB_OK)
         return st;
-    e = launch_batch_any(channels, bits, b, blend_radius, queue, max_levels,
+    e = launch_batch_any(channels, bits, b, blend_radius, th, queue, max_levels,
                          static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "sb_stylize_batch");
     return ok();
@@ -390,19 +395,25 @@ extern "C" sb_status sb_autotune_batch(const sb_frame *frames, int32_t n_frames,
     if (e != cudaSuccess) return cuda_fail(e, "sb_autotune_batch");
     if (cap != cudaStreamCaptureStatusNone)
         return fail(SB_ERR_INVALID_ARG, "sb_autotune_batch: the stream is being captured");
-    // every combination of the three choices; interleaving rows is tried only
-    // when the frames share one tile grid (otherwise it is frame order again)
-    bool same_grid = n_frames > 0 && n_frames <= kMaxBatch && frames;
-    for (int k = 1; k < n_frames && same_grid; ++k)
-        same_grid = (frames[k].tgt_guide.width + kTW - 1) / kTW ==
-                        (frames[0].tgt_guide.width + kTW - 1) / kTW &&
-                    (frames[k].tgt_guide.height + kTH - 1) / kTH ==
-                        (frames[0].tgt_guide.height + kTH - 1) / kTH;
-    sb_batch_schedule cand[8];
+    // every combination of the choices: tile heights 16, 32 and 64 (the other
+    // two only for blend radii up to 7), one CTA per tile or persistent, frame
+    // order or largest first, and tile rows interleaved when the frames share
+    // one tile grid (otherwise it is frame order again)
+    const bool ok_n = n_frames > 0 && n_frames <= kMaxBatch && frames;
+    sb_batch_schedule cand[24];
     int n_cand = 0;
-    for (int il = 0; il <= (same_grid ? 1 : 0); ++il)
-        for (int pers = 0; pers <= 1; ++pers)
-            for (int lf = 0; lf <= 1; ++lf) cand[n_cand++] = sb_batch_schedule{pers, lf, il};
+    for (int th : {32, 16, 64}) {
+        if (th != kTH && blend_radius > kMaxShapedRadius) continue;
+        bool same_grid = ok_n;
+        for (int k = 1; k < n_frames && same_grid; ++k)
+            same_grid = (frames[k].tgt_guide.width + kTW - 1) / kTW ==
+                            (frames[0].tgt_guide.width + kTW - 1) / kTW &&
+                        (frames[k].tgt_guide.height + th - 1) / th ==
+                            (frames[0].tgt_guide.height + th - 1) / th;
+        for (int il = 0; il <= (same_grid ? 1 : 0); ++il)
+            for (int pers = 0; pers <= 1; ++pers)
+                for (int lf = 0; lf <= 1; ++lf) cand[n_cand++] = sb_batch_schedule{pers, lf, il, th};
+    }
     cudaEvent_t ev[2];
     if ((e = cudaEventCreate(&ev[0])) != cudaSuccess) return cuda_fail(e, "sb_autotune_batch");
     if ((e = cudaEventCreate(&ev[1])) != cudaSuccess) {

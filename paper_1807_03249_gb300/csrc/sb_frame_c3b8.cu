@@ -1,12 +1,16 @@
-// Frame kernels instantiated for 8-bit guides with 3 channels.
+// Frame kernels and 32-row batch kernels of blend radii up to 7, instantiated
+// for 8-bit guides with 3 channels; the entry points of the format.
 #include "sb_frame.cuh"
 
 namespace sb {
 cudaError_t launch_frame_c3b8(int mode, const FrameArgs &a, cudaStream_t s) {
-    return launch_frame<3, 8>(mode, a, s);
+    if (mode == kStylize && a.radius > kNarrowMaxRadius) return launch_frame_wide_c3b8(a, s);
+    return launch_frame_narrow<3, 8>(mode, a, s);
 }
-cudaError_t launch_batch_c3b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
-                              cudaStream_t s) {
-    return launch_batch<3, 8>(b, r, max_levels, queue, s);
+cudaError_t launch_batch_c3b8(const BatchArgs &b, int r, int th, int max_levels,
+                              TileQueue *queue, cudaStream_t s) {
+    if (th != kTH) return launch_batch_shaped_c3b8(b, r, th, max_levels, queue, s);
+    if (r > kNarrowMaxRadius) return launch_batch_wide_c3b8(b, r, max_levels, queue, s);
+    return launch_batch32<3, 8, 0, kNarrowMaxRadius>(b, r, max_levels, queue, s);
 }
 }  // namespace sb

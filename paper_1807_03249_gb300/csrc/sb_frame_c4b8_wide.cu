@@ -1,0 +1,12 @@
+// Frame and batch kernels of blend radii 8-15, instantiated for 8-bit guides with 4 channels.
+#include "sb_frame.cuh"
+
+namespace sb {
+cudaError_t launch_frame_wide_c4b8(const FrameArgs &a, cudaStream_t s) {
+    return launch_stylize<4, 8, kNarrowMaxRadius + 1, kMaxFusedRadius>(a, s);
+}
+cudaError_t launch_batch_wide_c4b8(const BatchArgs &b, int r, int max_levels, TileQueue *queue,
+                                   cudaStream_t s) {
+    return launch_batch32<4, 8, kNarrowMaxRadius + 1, kMaxFusedRadius>(b, r, max_levels, queue, s);
+}
+}  // namespace sb

@@ -91,11 +91,16 @@ def test_invalid_blend_and_lut_arguments_are_rejected_on_the_host():
 def test_invalid_batch_and_schedule_arguments_are_rejected_on_the_host():
     lib = sb.load_library()
     frames = (sb._Frame * 1)()
-    sched = sb._Schedule(1, 1, 0)
+    sched = sb._Schedule(1, 1, 0, 0)
     best, ms = sb._Schedule(), ctypes.c_float()
     assert lib.sb_stylize_batch(frames, 129, 2, None) == -1            # too many frames
     assert lib.sb_stylize_batch(None, 1, 2, None) == -1                # NULL frames
     assert lib.sb_stylize_batch_sched(frames, 1, 16, ctypes.byref(sched), None) == -1  # radius
+    bad_rows = sb._Schedule(0, 0, 0, 48)
+    assert lib.sb_stylize_batch_sched(frames, 1, 2, ctypes.byref(bad_rows), None) == -1
+    assert b"tile_rows" in lib.sb_last_error()
+    tall = sb._Schedule(0, 0, 0, 64)
+    assert lib.sb_stylize_batch_sched(frames, 1, 9, ctypes.byref(tall), None) == -1  # r > 7
     assert lib.sb_stylize_batch_sched(frames, -1, 2, None, None) == -1
     assert lib.sb_stylize_batch_sched(frames, 0, 2, None, None) == 0   # empty batch: no-op
     assert lib.sb_autotune_batch(frames, 1, 2, 3, None, ctypes.byref(ms), None) == -1  # no best

@@ -149,17 +149,19 @@ def test_every_schedule_gives_the_same_pixels(cuda_device, radius):
     frames first: bit-identical outputs."""
     frames = _uneven_batch(cuda_device, 11, radius)
     ref = [o.clone() for o in sb.stylize_batch(frames, radius)]
-    for persistent in (0, 1):
-        for largest_first in (0, 1):
-            for f in frames:
-                f.out.zero_()
-            outs = sb.stylize_batch(frames, radius,
-                                    schedule={"persistent": persistent,
-                                              "largest_first": largest_first,
-                                              "interleave_rows": 1})  # mixed grids: frame order
-            torch.cuda.synchronize()
-            for k, (o, r) in enumerate(zip(outs, ref)):
-                assert torch.equal(o, r), f"schedule {persistent}{largest_first} frame {k}"
+    for rows in (32, 16, 64):
+        for persistent in (0, 1):
+            for largest_first in (0, 1):
+                for f in frames:
+                    f.out.zero_()
+                outs = sb.stylize_batch(frames, radius,
+                                        schedule={"persistent": persistent,
+                                                  "largest_first": largest_first,
+                                                  "interleave_rows": 1,  # mixed grids: frame order
+                                                  "tile_rows": rows})
+                torch.cuda.synchronize()
+                for k, (o, r) in enumerate(zip(outs, ref)):
+                    assert torch.equal(o, r), f"schedule {rows}/{persistent}{largest_first} frame {k}"
 
 
 @pytest.mark.parametrize("radius", [2, 3])
@@ -179,19 +181,22 @@ def test_interleaved_tile_rows_give_the_same_pixels(cuda_device, radius):
         frames.append(sb.BatchFrame(to_dev(g, cuda_device), e[4], e[3], levels, T, seed))
         hosts.append((g, e, levels, T, seed))
     ref = [o.clone() for o in sb.stylize_batch(frames, radius)]
-    for persistent in (0, 1):
-        for f in frames:
-            f.out.zero_()
-        outs = sb.stylize_batch(frames, radius, schedule={"persistent": persistent,
-                                                          "interleave_rows": 1})
-        torch.cuda.synchronize()
-        assert all(torch.equal(o, r) for o, r in zip(outs, ref)), f"persistent={persistent}"
+    for rows in (32, 16, 64):
+        for persistent in (0, 1):
+            for f in frames:
+                f.out.zero_()
+            outs = sb.stylize_batch(frames, radius, schedule={"persistent": persistent,
+                                                              "interleave_rows": 1,
+                                                              "tile_rows": rows})
+            torch.cuda.synchronize()
+            assert all(torch.equal(o, r) for o, r in zip(outs, ref)), f"{rows} rows, persistent={persistent}"
     for k in (0, 3):
         g, e, levels, T, seed = hosts[k]
         want, _, _ = oracle.stylize(g, e[0], e[1], 5, levels, T, radius, seed)
         assert np.array_equal(ref[k].cpu().numpy(), want)
     best, _ = sb.autotune_batch(frames, radius, reps=1)
-    assert set(best) == {"persistent", "largest_first", "interleave_rows"}
+    assert set(best) == {"persistent", "largest_first", "interleave_rows", "tile_rows"}
+    assert best["tile_rows"] in (16, 32, 64)
 
 
 def test_persistent_queue_resets_across_launches_and_graph_replays(cuda_device):
@@ -281,14 +286,16 @@ def test_every_schedule_gives_the_same_pixels_uv16(cuda_device):
         frames.append(sb.BatchFrame(to_dev(g, cuda_device), lut, st, int(rng.integers(2, 8)),
                                     int(rng.integers(0, 1 << 21)), int(rng.integers(0, 2**32))))
     ref = [o.clone() for o in sb.stylize_batch(frames, 3)]
-    for persistent in (0, 1):
-        for largest_first in (0, 1):
-            for f in frames:
-                f.out.zero_()
-            sb.stylize_batch(frames, 3, schedule={"persistent": persistent,
-                                                  "largest_first": largest_first})
-            torch.cuda.synchronize()
-            assert all(torch.equal(f.out, r) for f, r in zip(frames, ref))
+    for rows in (32, 16, 64):
+        for persistent in (0, 1):
+            for largest_first in (0, 1):
+                for f in frames:
+                    f.out.zero_()
+                sb.stylize_batch(frames, 3, schedule={"persistent": persistent,
+                                                      "largest_first": largest_first,
+                                                      "tile_rows": rows})
+                torch.cuda.synchronize()
+                assert all(torch.equal(f.out, r) for f, r in zip(frames, ref)), (rows, persistent)
     # and one frame against the oracle
     f0 = frames[0]
     g0 = f0.tgt_guide.cpu().numpy().view(np.uint16)
