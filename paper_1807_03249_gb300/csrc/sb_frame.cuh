@@ -26,8 +26,8 @@
 //            Work goes by vertical segments of 4 pixels, one region column per
 //            lane: a segment lies in one cell at levels >= 2 and the keys are
 //            affine in p, so its four keys per cell are one multiply-add and
-//            three adds.  Segments with rejected pixels are compacted into the
-//            next level's list.
+//            three adds.  Each warp compacts the segments it rejected into a
+//            list of its own and takes them down the levels by itself.
 //   vote     ballots mark, per region row, where A steps by exactly one pixel
 //            (E, horizontally) and where it continues the row above (V); one
 //            thread per row turns them into 64-bit masks of the output columns
@@ -143,18 +143,6 @@ __host__ __device__ constexpr bool vote_masks_fit(int r, int th) {
 }
 static_assert(vote_masks_fit(0, 16) && vote_masks_fit(0, 32) && vote_masks_fit(0, 64),
               "the vote masks fit in the region guide's shared memory");
-
-// Block-wide append to a shared list; every lane of the warp must call it.
-__device__ __forceinline__ void list_push(bool pred, int val, uint16_t *list, int *counter) {
-    const unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
-    if (mask == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(counter, __popc(mask));
-    base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    if (pred) list[base + __popc(mask & ((1u << lane) - 1u))] = (uint16_t)val;
-}
 
 // Seed cells of level l for the clamped region [xa, xb] x [ya, yb].
 struct LevelCells {
@@ -470,41 +458,6 @@ __device__ __forceinline__ uint32_t segment_level(const FrameArgs &a, const uint
     return test_segment<C, B, RW>(sv, gt, A, lev, l, t32, m, ibase, v);
 }
 
-// One level over segments: the top level (top) visits every segment of the region
-// (its in-target pixels), lower levels the list of segments with pending
-// pixels (entries: segment index << 4 | pixel mask).  Segments with rejected
-// pixels are appended to list_out.
-template <int C, int B, int R, int TH>
-__device__ __forceinline__ void level_segments(const FrameArgs &a, const uint32_t *gt,
-                                               uint32_t *A, uint8_t *lev, const int4 *cells,
-                                               int base, const LevelCells &g, int l, int rx0,
-                                               int ry0, const TileBounds &tb, uint32_t t32,
-                                               bool top, const uint16_t *list_in, int n_in,
-                                               uint16_t *list_out, int *cnt_out) {
-    using S = Segs<R, TH>;
-    const int n = top ? S::NS : n_in;
-    for (int s0 = 0; s0 < n; s0 += Tile<TH>::Threads) {
-        const int jj = s0 + (int)threadIdx.x;
-        int sg = 0;
-        uint32_t m = 0;
-        if (jj < n) {
-            if (top) {
-                sg = jj;
-                m = tb.template mask<R, TH>(S::rx(sg), S::ry(sg));
-            } else {
-                const uint32_t e = list_in[jj];
-                sg = (int)(e >> 4);
-                m = e & 15u;
-            }
-        }
-        uint32_t rej = 0;
-        if (m)
-            rej = segment_level<C, B, R, TH>(a, gt, A, lev, cells, base, g, l, rx0, ry0, t32,
-                                         S::rx(sg), S::ry(sg), m);
-        list_push(rej != 0, (sg << 4) | (int)rej, list_out, cnt_out);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // assignment of the region held in shared memory (Algorithm 2)
 // ---------------------------------------------------------------------------
@@ -519,7 +472,6 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     uint32_t *A = reinterpret_cast<uint32_t *>(smem + L.off_A);
     uint16_t *const list0 = reinterpret_cast<uint16_t *>(smem + L.off_list0);
     uint16_t *const list1 = reinterpret_cast<uint16_t *>(smem + L.off_list1);
-    int *cnt = reinterpret_cast<int *>(smem + L.off_cnt);
     const int tid = threadIdx.x;
 
     const int xa = max(rx0, 0), xb = min(rx0 + RW, a.W) - 1;
@@ -530,10 +482,6 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     const int eager_lo = L_top <= kEagerMinLevel ? 1 : kEagerMinLevel;
     const TileBounds tb = TileBounds::of<R, TH>(rx0, ry0, a.W, a.H);
 
-    if (tid == 0) {
-        cnt[0] = 0;
-        cnt[1] = 0;
-    }
     // phase 0: every global load (the guide at this thread's seed, the
     // region's guide, then the seed's table entry) is issued before the
     // first store that waits on one.  Thread k builds eager cell k (levels
@@ -597,30 +545,66 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
                                     n_eager);
     __syncthreads();
 
-    // level step t (0 = top) appends to counter t % 3; the counter of step
-    // t + 1 is cleared during step t (its last reader passed step t - 1's
-    // barrier), so one barrier per level publishes both the list and the reset.
-    // The top level visits every segment of the region; its cells start at 0.
-    int n_pend = Segs<R, TH>::NS, base = 0;
-    const uint16_t *list_cur = list0;
-    uint16_t *list_nxt = list1;
-    for (int l = L_top, t = 0; l >= 1 && n_pend > 0; --l, ++t) {
-        const LevelCells g = level_cells(l, xa, xb, ya, yb);
+    // The top level visits every segment of the region, thread by thread as
+    // the block's segments fall (warp w takes 32 consecutive segments of each
+    // round); every warp keeps the segments it rejected (entries: segment
+    // index << 4 | pixel mask) in a list of its own and takes them down the
+    // eager levels by itself, compacting with ballots: no block barrier and no
+    // shared counter between those levels.  Levels 2 and 1 need their cells
+    // built by the whole block first, and only if some warp still holds a
+    // pixel.
+    using S = Segs<R, TH>;
+    constexpr int kWarpCap = (S::NS + kThreads - 1) / kThreads * 32;
+    const int warp = tid >> 5, lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    uint16_t *wl_cur = list0 + warp * kWarpCap, *wl_nxt = list1 + warp * kWarpCap;
+    int n_w = 0, base = 0;
+    {
+        const LevelCells g = level_cells(L_top, xa, xb, ya, yb);
+        for (int s0 = 0; s0 < S::NS; s0 += kThreads) {
+            const int sg = s0 + tid;
+            const uint32_t m = sg < S::NS ? tb.template mask<R, TH>(S::rx(sg), S::ry(sg)) : 0u;
+            uint32_t rej = 0;
+            if (m)
+                rej = segment_level<C, B, R, TH>(a, gt, A, lev, cells, base, g, L_top, rx0, ry0,
+                                                 t32, S::rx(sg), S::ry(sg), m);
+            const unsigned mk = __ballot_sync(0xFFFFFFFFu, rej != 0);
+            if (rej) wl_cur[n_w + __popc(mk & lt)] = (uint16_t)((sg << 4) | (int)rej);
+            n_w += __popc(mk);
+        }
+        base += g.ncx * g.ncy;
+    }
+    for (int l = L_top - 1; l >= 1; --l) {
         if (l == kEagerMinLevel - 1 && eager_lo > 1) {
-            // a pixel still needs the fine levels: build levels 2 and 1 now
+            // levels 2 and 1: the block builds their cells, and only if some
+            // warp still holds a pixel (every thread reaches this point)
+            if (!__syncthreads_or(n_w > 0)) break;
             build_cells<C, B, kThreads>(a, cells, l, 1, base, xa, xb, ya, yb, cxo, cyo);
             __syncthreads();
         }
-        if (tid == 0) cnt[(t + 1) % 3] = 0;
-        level_segments<C, B, R, TH>(a, gt, A, lev, cells, base, g, l, rx0, ry0, tb, t32, t == 0,
-                                    list_cur, n_pend, list_nxt, &cnt[t % 3]);
-        __syncthreads();
-        n_pend = cnt[t % 3];
+        const LevelCells g = level_cells(l, xa, xb, ya, yb);
+        // n_w is the same in every lane of the warp
+        int n_next = 0;
+        for (int j0 = 0; j0 < n_w; j0 += 32) {
+            const uint32_t e = j0 + lane < n_w ? wl_cur[j0 + lane] : 0u;
+            const uint32_t m = e & 15u;
+            const int sg = (int)(e >> 4);
+            uint32_t rej = 0;
+            if (m)
+                rej = segment_level<C, B, R, TH>(a, gt, A, lev, cells, base, g, l, rx0, ry0, t32,
+                                                 S::rx(sg), S::ry(sg), m);
+            const unsigned mk = __ballot_sync(0xFFFFFFFFu, rej != 0);
+            if (rej) wl_nxt[n_next + __popc(mk & lt)] = (uint16_t)((sg << 4) | (int)rej);
+            n_next += __popc(mk);
+        }
+        __syncwarp();
+        uint16_t *const t = wl_cur;
+        wl_cur = wl_nxt;
+        wl_nxt = t;
+        n_w = n_next;
         base += g.ncx * g.ncy;
-        const uint16_t *done = list_cur;
-        list_cur = list_nxt;
-        list_nxt = const_cast<uint16_t *>(done);
     }
+    __syncthreads();  // the region's A is complete before the vote reads it
 }
 
 // ---------------------------------------------------------------------------
