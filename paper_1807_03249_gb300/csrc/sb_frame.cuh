@@ -104,9 +104,17 @@ struct SmemLayout {
     size_t off_cells, off_gt, off_A, off_list0, off_list1, off_bytes, off_masks, off_cnt, total;
 };
 
-// Shared memory of one tile.  The vote's masks overlay the target guide of
-// the region, which is dead once the assignment is done; the level bytes exist
-// only for the assignment-only kernel (the fused path never stores levels).
+// Bytes of the vote's masks: per region row E, V, N (4 words each) and the
+// 64-bit output-column masks hu, t2, vc, ni; per output row U, T2, NI.
+__host__ __device__ constexpr size_t vote_mask_bytes(int r, int th) {
+    return (size_t)(3 * 4 * 4 + 4 * 8) * (th + 2 * r) + (size_t)3 * 8 * th;
+}
+
+// Shared memory of one tile.  Once the assignment is done the seed cells and
+// the region's target guide are dead: the vote lays its masks over the cells
+// (the area is at least as large as the masks) and the source texel index of
+// each region pixel's assignment over the guide.  The level bytes exist only
+// for the assignment-only kernel (the fused path never stores levels).
 __host__ __device__ inline SmemLayout smem_layout(int r, int levels, bool level_bytes = false,
                                                   int th = kTH) {
     SmemLayout s;
@@ -117,11 +125,10 @@ __host__ __device__ inline SmemLayout smem_layout(int r, int levels, bool level_
     for (int l = 1; l <= levels; ++l) s.NC += cells_bound(s.RW, s.RH, l);
     size_t o = 0;
     s.off_cells = o;
-    o += sizeof(int4) * (size_t)s.NC;
-    s.off_gt = o;
-    // vote masks: per region row E, V (4 words each), hu, t2, vc (64-bit);
-    // per output row U, T2 (64-bit); they fit in the guide's 4 NR bytes
     s.off_masks = o;
+    const size_t cell_bytes = sizeof(int4) * (size_t)s.NC, mask_bytes = vote_mask_bytes(r, th);
+    o += (cell_bytes > mask_bytes ? cell_bytes : ((mask_bytes + 15) & ~(size_t)15));
+    s.off_gt = o;
     o += sizeof(uint32_t) * (size_t)s.NR;
     s.off_A = o;
     o += sizeof(uint32_t) * (size_t)s.NR;
@@ -137,12 +144,6 @@ __host__ __device__ inline SmemLayout smem_layout(int r, int levels, bool level_
     s.total = o;
     return s;
 }
-__host__ __device__ constexpr bool vote_masks_fit(int r, int th) {
-    return (8 * 4 + 3 * 8) * (th + 2 * r) + 2 * 8 * th <= 4 * (kTW + 2 * r) * (th + 2 * r) &&
-           (r == 15 || vote_masks_fit(r + 1, th));
-}
-static_assert(vote_masks_fit(0, 16) && vote_masks_fit(0, 32) && vote_masks_fit(0, 64),
-              "the vote masks fit in the region guide's shared memory");
 
 // Seed cells of level l for the clamped region [xa, xb] x [ya, yb].
 struct LevelCells {
@@ -626,9 +627,13 @@ template <>
 struct VoteAcc<true> {
     uint32_t lo = 0, hi = 0, n = 0;  // lo = c0 | c2 << 16, hi = c1 | c3 << 16
     __device__ __forceinline__ void add(uint32_t col, uint32_t cnt) {
-        lo += (col & 0x00FF00FFu) * cnt;
-        hi += ((col >> 8) & 0x00FF00FFu) * cnt;
+        sum(col, cnt);
         n += cnt;
+    }
+    // cnt taps of colour col, the count kept by the caller
+    __device__ __forceinline__ void sum(uint32_t col, uint32_t cnt) {
+        lo += (col & 0x00FF00FFu) * cnt;
+        hi += __byte_perm(col, 0u, 0x4341u) * cnt;  // bytes 1 and 3 into the low halves
     }
     __device__ __forceinline__ void sums(uint32_t &s0, uint32_t &s1, uint32_t &s2,
                                          uint32_t &s3) const {
@@ -643,11 +648,14 @@ template <>
 struct VoteAcc<false> {
     uint32_t s[4] = {0, 0, 0, 0}, n = 0;
     __device__ __forceinline__ void add(uint32_t col, uint32_t cnt) {
+        sum(col, cnt);
+        n += cnt;
+    }
+    __device__ __forceinline__ void sum(uint32_t col, uint32_t cnt) {
         s[0] += (col & 0xFFu) * cnt;
         s[1] += ((col >> 8) & 0xFFu) * cnt;
         s[2] += ((col >> 16) & 0xFFu) * cnt;
         s[3] += (col >> 24) * cnt;
-        n += cnt;
     }
     __device__ __forceinline__ void sums(uint32_t &s0, uint32_t &s1, uint32_t &s2,
                                          uint32_t &s3) const {
@@ -710,9 +718,12 @@ struct StyleView {
     __device__ __forceinline__ bool in_source(uint32_t v) const {
         return (v & 0xFFFFu) < Ws && v < Hs16;
     }
-    __device__ __forceinline__ uint32_t at(uint32_t v) const {
-        return __ldg(style32 + ((v >> 16) * stride + (v & 0xFFFFu)));
+    __device__ __forceinline__ uint32_t at(uint32_t v) const { return texel(lin(v)); }
+    // texel index y * stride + x of the packed source position v = x | y << 16
+    __device__ __forceinline__ uint32_t lin(uint32_t v) const {
+        return (v >> 16) * stride + (v & 0xFFFFu);
     }
+    __device__ __forceinline__ uint32_t texel(uint32_t i) const { return __ldg(style32 + i); }
     // cnt taps whose source position is v (nothing when cnt == 0 or v is
     // outside the source)
     template <typename Acc>
@@ -733,52 +744,79 @@ __device__ __forceinline__ uint32_t window_steps(const uint32_t *E, int ry, int 
     return __funnelshift_r(e[b >> 5], e[(b >> 5) + 1], b & 31) & kM;
 }
 
-// Windows whose rows have at most two runs each: one gather per run (the
-// second has length 0 in a single-run row).
+// Windows whose rows have at most two runs each and whose taps all come from
+// interior assignments (every tap lies in the source, so the window counts
+// all (2R + 1)^2 taps): one gather per run (the second has length 0 in a
+// single-run row).  T holds the texel index of each region pixel's
+// assignment; tap o = (ox, oy) of a window reads texel T(p + o) - ox - oy S.
 template <int R, bool F32, int NT>
 __device__ __forceinline__ void vote_two_runs(const FrameArgs &a, const StyleView &sv,
-                                              const uint32_t *A, const uint32_t *E,
+                                              const uint32_t *T, const uint32_t *E,
                                               const uint16_t *list, int n, int x0, int y0) {
     constexpr int RW = kTW + 2 * R;
     constexpr bool kPacked = (2 * R + 1) * (2 * R + 1) * 255 < 65536;
+    constexpr uint32_t kFull = (2 * R + 1) * (2 * R + 1);
+    const uint32_t S = sv.stride;
     for (int j = threadIdx.x; j < n; j += NT) {
         const int k = list[j];
         const int tx = k % kTW, ty = k / kTW;
         VoteAcc<kPacked> acc;
+        uint32_t rb = (uint32_t)R + (uint32_t)R * S;  // R - oy S
         // windows above 15 x 15 (one CTA per SM, rarely used) stay rolled
         constexpr int kUnroll = R <= 7 ? 2 * R + 1 : 1;
 #pragma unroll kUnroll
         for (int oy = -R; oy <= R; ++oy) {
             const int ry = ty + R + oy;
-            const uint32_t *row = A + ry * RW;
-            const int j1 = __ffs(~window_steps<R>(E, ry, tx));  // first run: taps [0, j1)
-            sv.add(acc, tap_pos(row[tx], -R, oy), (uint32_t)j1);
-            const int c2 = min(tx + j1, tx + 2 * R);
-            sv.add(acc, tap_pos(row[c2], c2 - tx - R, oy), (uint32_t)(2 * R + 1 - j1));
+            const uint32_t *row = T + ry * RW + tx;
+            const uint32_t j1 = __ffs(~window_steps<R>(E, ry, tx));  // first run: taps [0, j1)
+            acc.sum(sv.texel(row[0] + rb), j1);
+            const uint32_t d = min(j1, 2u * R);
+            acc.sum(sv.texel(row[d] + rb - d), 2u * R + 1u - j1);
+            rb -= S;
         }
+        acc.n = kFull;
         vote_store<F32, R>(a, acc, x0 + tx, y0 + ty);
     }
 }
 
-// Every other window (junctions of three or more chunks, frame borders): tap
-// by tap.  The block's such pixels share one list.
+// Every other window (junctions of three or more chunks, frame borders and
+// taps near the source border): tap by tap.  The block's such pixels share
+// one list; an entry's top bit marks a window whose taps all come from
+// interior assignments, which skips the per-tap source test.
+constexpr uint16_t kInteriorFlag = 0x8000u;
+
 template <int R, bool F32, int NT>
 __device__ __forceinline__ void vote_taps(const FrameArgs &a, const StyleView &sv,
-                                          const uint32_t *A, const uint16_t *list, int n, int x0,
-                                          int y0) {
+                                          const uint32_t *A, const uint32_t *T,
+                                          const uint16_t *list, int n, int x0, int y0) {
     constexpr int RW = kTW + 2 * R;
     constexpr bool kPacked = (2 * R + 1) * (2 * R + 1) * 255 < 65536;
+    constexpr uint32_t kFull = (2 * R + 1) * (2 * R + 1);
+    constexpr int kUnroll = R <= 7 ? 2 * R + 1 : 1;
+    const uint32_t S = sv.stride;
     for (int j = threadIdx.x; j < n; j += NT) {
-        const int k = list[j];
+        const int e = list[j];
+        const int k = e & ~(int)kInteriorFlag;
         const int tx = k % kTW, ty = k / kTW;
         VoteAcc<kPacked> acc;
-        for (int oy = -R; oy <= R; ++oy) {
-            const uint32_t *row = A + (ty + R + oy) * RW + tx + R;
-            constexpr int kUnroll = R <= 7 ? 2 * R + 1 : 1;
+        if (e & kInteriorFlag) {
+            uint32_t rb = (uint32_t)R * S;  // -oy S
+            for (int oy = -R; oy <= R; ++oy) {
+                const uint32_t *row = T + (ty + R + oy) * RW + tx + R;
 #pragma unroll kUnroll
-            for (int ox = -R; ox <= R; ++ox) sv.add(acc, tap_pos(row[ox], ox, oy), 1u);
+                for (int ox = -R; ox <= R; ++ox) acc.sum(sv.texel(row[ox] + rb - (uint32_t)ox), 1u);
+                rb -= S;
+            }
+            acc.n = kFull;
+            vote_store<F32, R>(a, acc, x0 + tx, y0 + ty);
+        } else {
+            for (int oy = -R; oy <= R; ++oy) {
+                const uint32_t *row = A + (ty + R + oy) * RW + tx + R;
+#pragma unroll kUnroll
+                for (int ox = -R; ox <= R; ++ox) sv.add(acc, tap_pos(row[ox], ox, oy), 1u);
+            }
+            vote_store<F32, R>(a, acc, x0 + tx, y0 + ty);
         }
-        vote_store<F32, R>(a, acc, x0 + tx, y0 + ty);
     }
 }
 
@@ -787,26 +825,32 @@ __device__ __forceinline__ uint64_t shr128(uint64_t lo, uint64_t hi, int j) {
     return j == 0 ? lo : ((lo >> j) | (hi << (64 - j)));
 }
 
-// Shared-memory words of the vote's masks: per region row E (4 words), V (4
-// words) and the 64-bit output-column masks hu, t2, vc; per output row the
-// 64-bit class masks U and T2.
+// Shared-memory words of the vote's masks: per region row E, V, N (4 words
+// each) and the 64-bit output-column masks hu, t2, vc, ni; per output row the
+// 64-bit class masks U, T2, NI.
 template <int R, int TH>
 struct VoteMasks {
     static constexpr int RH = TH + 2 * R;
-    uint32_t *E, *V;
-    uint64_t *hu, *t2, *vc, *U, *T2;
+    uint32_t *E, *V, *N;
+    uint64_t *hu, *t2, *vc, *ni, *U, *T2, *NI;
     __device__ __forceinline__ static VoteMasks at(unsigned char *p) {
         VoteMasks m;
         m.E = reinterpret_cast<uint32_t *>(p);
         m.V = m.E + 4 * RH;
-        m.hu = reinterpret_cast<uint64_t *>(m.V + 4 * RH);
+        m.N = m.V + 4 * RH;
+        m.hu = reinterpret_cast<uint64_t *>(m.N + 4 * RH);
         m.t2 = m.hu + RH;
         m.vc = m.t2 + RH;
-        m.U = m.vc + RH;
+        m.ni = m.vc + RH;
+        m.U = m.ni + RH;
         m.T2 = m.U + TH;
+        m.NI = m.T2 + TH;
         return m;
     }
 };
+
+// texel index of a region pixel without an assignment in the source
+constexpr uint32_t kNoTexel = 0xFFFFFFFFu;
 
 template <int R, bool F32, int TH>
 __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &L, int x0,
@@ -816,67 +860,88 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const StyleView sv = StyleView::of(a);
     const VoteMasks<R, TH> mk = VoteMasks<R, TH>::at(smem + L.off_masks);
+    uint32_t *const T = reinterpret_cast<uint32_t *>(smem + L.off_gt);
     if (R > 0 && threadIdx.x == 0) {
         int *cnt = reinterpret_cast<int *>(smem + L.off_cnt);
         cnt[3] = cnt[4] = 0;  // two-runs and tap-by-tap list lengths
     }
 
     if constexpr (R > 0) {
-        // per region row: E bit x <=> A[x] == A[x-1] + 1, V bit x <=>
-        // A[ry][x] == A[ry-1][x] + (0, 1) (never true next to kInvalid)
+        // per region pixel: T = texel index of A (kNoTexel outside the
+        // source); per region row: E bit x <=> A[x] == A[x-1] + 1, V bit x
+        // <=> A[ry][x] == A[ry-1][x] + (0, 1) (never true next to kInvalid),
+        // N bit x <=> A[x] lies at least R pixels inside the source, so every
+        // tap it gives a window lies in the source
+        const uint32_t iw = sv.Ws > 2u * R ? sv.Ws - 2u * R : 0u;
+        const uint32_t ih16 = (sv.Hs16 >> 16) > 2u * R ? sv.Hs16 - (2u * R << 16) : 0u;
+        constexpr uint32_t kRR = (uint32_t)R | ((uint32_t)R << 16);
         for (int ry = warp; ry < RH; ry += kWarps) {
             const uint32_t *row = A + ry * RW;
+            uint32_t *trow = T + ry * RW;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const int x = c * 32 + lane;
-                bool eb = false, vb = false;
+                bool eb = false, vb = false, nb = false;
                 if (x < RW) {
                     const uint32_t cur = row[x];
                     eb = x >= 1 && cur == row[x - 1] + 1u;
                     vb = ry >= 1 && cur == row[x - RW] + 0x10000u;
+                    // x - R borrows from y when x < R, which leaves the
+                    // low half at or above 65536 - R > iw
+                    const uint32_t d = cur - kRR;
+                    nb = (d & 0xFFFFu) < iw && d < ih16;
+                    trow[x] = sv.in_source(cur) ? sv.lin(cur) : kNoTexel;
                 }
                 const uint32_t e = __ballot_sync(0xFFFFFFFFu, eb);
                 const uint32_t v = __ballot_sync(0xFFFFFFFFu, vb);
+                const uint32_t nn = __ballot_sync(0xFFFFFFFFu, nb);
                 if (lane == 0) {
                     mk.E[4 * ry + c] = e;
                     mk.V[4 * ry + c] = v;
+                    mk.N[4 * ry + c] = nn;
                 }
             }
-            if (lane == 0) mk.E[4 * ry + 3] = mk.V[4 * ry + 3] = 0u;
+            if (lane == 0) mk.E[4 * ry + 3] = mk.V[4 * ry + 3] = mk.N[4 * ry + 3] = 0u;
         }
         __syncthreads();
         // one thread per region row, 64 output columns at once: hu bit tx <=>
         // window row tx..tx+2R is one run; t2 <=> at most two runs; vc <=> the
-        // centre column is linked to the row above
+        // centre column is linked to the row above; ni <=> every pixel of the
+        // window row is interior
         if (threadIdx.x < RH) {
             const int ry = threadIdx.x;
-            const uint32_t *e = mk.E + 4 * ry, *v = mk.V + 4 * ry;
+            const uint32_t *e = mk.E + 4 * ry, *v = mk.V + 4 * ry, *nw = mk.N + 4 * ry;
             const uint64_t blo = ~((uint64_t)e[0] | ((uint64_t)e[1] << 32)), bhi = ~(uint64_t)e[2];
-            uint64_t seen = 0, two = 0;
+            const uint64_t ilo = (uint64_t)nw[0] | ((uint64_t)nw[1] << 32), ihi = nw[2];
+            uint64_t seen = 0, two = 0, in = ilo;
             constexpr int kUnroll = R <= 7 ? 2 * R : 1;
 #pragma unroll kUnroll
             for (int s = 1; s <= 2 * R; ++s) {
                 const uint64_t b = shr128(blo, bhi, s);
                 two |= seen & b;
                 seen |= b;
+                in &= shr128(ilo, ihi, s);
             }
             mk.hu[ry] = ~seen;
             mk.t2[ry] = ~two;
             mk.vc[ry] = shr128((uint64_t)v[0] | ((uint64_t)v[1] << 32), v[2], R);
+            mk.ni[ry] = in;
         }
         __syncthreads();
-        // one thread per output row: uniform windows (one translation) and
-        // windows whose rows have at most two runs
+        // one thread per output row: uniform windows (one translation),
+        // interior windows whose rows have at most two runs, interior windows
         if (threadIdx.x < TH) {
             const int ty = threadIdx.x;
-            uint64_t U = mk.hu[ty], T2 = mk.t2[ty];
+            uint64_t U = mk.hu[ty], T2 = mk.t2[ty], NI = mk.ni[ty];
 #pragma unroll
             for (int k = 1; k <= 2 * R; ++k) {
                 U &= mk.hu[ty + k] & mk.vc[ty + k];
                 T2 &= mk.t2[ty + k];
+                NI &= mk.ni[ty + k];
             }
             mk.U[ty] = U;
-            mk.T2[ty] = T2 & ~U;
+            mk.T2[ty] = T2 & NI & ~U;
+            mk.NI[ty] = NI;
         }
         __syncthreads();
     }
@@ -900,8 +965,13 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
             const int tx = c * 32 + lane;
             col[q][c] = 0;
             if ((U >> tx) & 1ull) {
-                const uint32_t v = A[(ty + R) * RW + tx + R];
-                if (sv.in_source(v)) col[q][c] = sv.at(v);
+                if constexpr (R > 0) {
+                    const uint32_t i = T[(ty + R) * RW + tx + R];
+                    if (i != kNoTexel) col[q][c] = sv.texel(i);
+                } else {
+                    const uint32_t v = A[ty * RW + tx];
+                    if (sv.in_source(v)) col[q][c] = sv.at(v);
+                }
             }
         }
     }
@@ -929,7 +999,7 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
         int *cnt = reinterpret_cast<int *>(smem + L.off_cnt);
         uint16_t *glist = reinterpret_cast<uint16_t *>(smem + L.off_list0);
         uint16_t *tlist = reinterpret_cast<uint16_t *>(smem + L.off_list1);
-        uint64_t Gm[kRowsPerWarp], Tm[kRowsPerWarp];
+        uint64_t Gm[kRowsPerWarp], Tm[kRowsPerWarp], Im[kRowsPerWarp];
         int n_g = 0, n_t = 0;
 #pragma unroll
         for (int q = 0; q < kRowsPerWarp; ++q) {
@@ -937,6 +1007,7 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
             const uint64_t in = y0 + ty < a.H ? incols : 0ull;
             Gm[q] = mk.T2[ty] & in;
             Tm[q] = ~mk.U[ty] & ~mk.T2[ty] & in;
+            Im[q] = mk.NI[ty];
             n_g += __popcll(Gm[q]);
             n_t += __popcll(Tm[q]);
         }
@@ -955,15 +1026,17 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
             for (int c = 0; c < 2; ++c) {
                 const int k = ty * kTW + c * 32 + lane;
                 const uint32_t mg = (uint32_t)(Gm[q] >> (32 * c)), mt = (uint32_t)(Tm[q] >> (32 * c));
+                const uint32_t mi = (uint32_t)(Im[q] >> (32 * c));
                 if ((mg >> lane) & 1u) glist[bg + __popc(mg & lt)] = (uint16_t)k;
-                if ((mt >> lane) & 1u) tlist[bt + __popc(mt & lt)] = (uint16_t)k;
+                if ((mt >> lane) & 1u)
+                    tlist[bt + __popc(mt & lt)] = (uint16_t)(k | ((mi >> lane) & 1u ? kInteriorFlag : 0));
                 bg += __popc(mg);
                 bt += __popc(mt);
             }
         }
         __syncthreads();
-        vote_two_runs<R, F32, kThreads>(a, sv, A, mk.E, glist, cnt[3], x0, y0);
-        vote_taps<R, F32, kThreads>(a, sv, A, tlist, cnt[4], x0, y0);
+        vote_two_runs<R, F32, kThreads>(a, sv, T, mk.E, glist, cnt[3], x0, y0);
+        vote_taps<R, F32, kThreads>(a, sv, A, T, tlist, cnt[4], x0, y0);
     }
 }
 
