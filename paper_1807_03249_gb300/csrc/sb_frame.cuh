@@ -852,7 +852,41 @@ struct VoteMasks {
 // texel index of a region pixel without an assignment in the source
 constexpr uint32_t kNoTexel = 0xFFFFFFFFu;
 
-template <int R, bool F32, int TH>
+// Step, link and interior bits of region pixel x of row ry (x >= 1 or
+// ry >= 1 may fail at the region's first column or row), and its texel index.
+template <int R, int RW, bool kTrustA>
+__device__ __forceinline__ void pixel_bits(const uint32_t *A, uint32_t *T, const StyleView &sv,
+                                           uint32_t iw, uint32_t ih16, int ry, int x, bool &eb,
+                                           bool &vb, bool &nb) {
+    constexpr uint32_t kRR = (uint32_t)R | ((uint32_t)R << 16);
+    const int i = ry * RW + x;
+    const uint32_t cur = A[i];
+    eb = x >= 1 && cur == A[i - 1] + 1u;
+    vb = ry >= 1 && cur == A[i - RW] + 0x10000u;
+    // x - R borrows from y when x < R, which leaves the low half at or above
+    // 65536 - R > iw
+    const uint32_t d = cur - kRR;
+    nb = (d & 0xFFFFu) < iw && d < ih16;
+    // the fused kernels assign every target pixel a source position and mark
+    // the rest kInvalid; assignments read from memory may be anything
+    const bool ok = kTrustA ? cur != kInvalid : sv.in_source(cur);
+    T[i] = ok ? sv.lin(cur) : kNoTexel;
+}
+
+// Exclusive prefix over the warp of v, and the warp's total in *tot.
+__device__ __forceinline__ int warp_exclusive_scan(int v, int &tot) {
+    const int lane = threadIdx.x & 31;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    tot = __shfl_sync(0xFFFFFFFFu, x, 31);
+    return x - v;
+}
+
+template <int R, bool F32, int TH, bool kTrustA = true>
 __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &L, int x0,
                                           int y0, const uint32_t *A, unsigned char *smem) {
     constexpr int RW = kTW + 2 * R, RH = TH + 2 * R;
@@ -861,10 +895,12 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
     const StyleView sv = StyleView::of(a);
     const VoteMasks<R, TH> mk = VoteMasks<R, TH>::at(smem + L.off_masks);
     uint32_t *const T = reinterpret_cast<uint32_t *>(smem + L.off_gt);
-    if (R > 0 && threadIdx.x == 0) {
-        int *cnt = reinterpret_cast<int *>(smem + L.off_cnt);
-        cnt[3] = cnt[4] = 0;  // two-runs and tap-by-tap list lengths
-    }
+    int *const cnt = reinterpret_cast<int *>(smem + L.off_cnt);
+    uint16_t *const glist = reinterpret_cast<uint16_t *>(smem + L.off_list0);
+    uint16_t *const tlist = reinterpret_cast<uint16_t *>(smem + L.off_list1);
+    const int wcols = min(a.W - x0, kTW);  // columns of the tile inside the target
+    const uint64_t incols = wcols >= 64 ? ~0ull : ((1ull << wcols) - 1ull);
+    if (R > 0 && threadIdx.x == 0) cnt[3] = cnt[4] = 0;  // two-runs and tap-by-tap list lengths
 
     if constexpr (R > 0) {
         // per region pixel: T = texel index of A (kNoTexel outside the
@@ -874,24 +910,12 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
         // tap it gives a window lies in the source
         const uint32_t iw = sv.Ws > 2u * R ? sv.Ws - 2u * R : 0u;
         const uint32_t ih16 = (sv.Hs16 >> 16) > 2u * R ? sv.Hs16 - (2u * R << 16) : 0u;
-        constexpr uint32_t kRR = (uint32_t)R | ((uint32_t)R << 16);
+        // columns 0..63: a warp per row, 32 columns per ballot
         for (int ry = warp; ry < RH; ry += kWarps) {
-            const uint32_t *row = A + ry * RW;
-            uint32_t *trow = T + ry * RW;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int x = c * 32 + lane;
-                bool eb = false, vb = false, nb = false;
-                if (x < RW) {
-                    const uint32_t cur = row[x];
-                    eb = x >= 1 && cur == row[x - 1] + 1u;
-                    vb = ry >= 1 && cur == row[x - RW] + 0x10000u;
-                    // x - R borrows from y when x < R, which leaves the
-                    // low half at or above 65536 - R > iw
-                    const uint32_t d = cur - kRR;
-                    nb = (d & 0xFFFFu) < iw && d < ih16;
-                    trow[x] = sv.in_source(cur) ? sv.lin(cur) : kNoTexel;
-                }
+            for (int c = 0; c < 2; ++c) {
+                bool eb, vb, nb;
+                pixel_bits<R, RW, kTrustA>(A, T, sv, iw, ih16, ry, c * 32 + lane, eb, vb, nb);
                 const uint32_t e = __ballot_sync(0xFFFFFFFFu, eb);
                 const uint32_t v = __ballot_sync(0xFFFFFFFFu, vb);
                 const uint32_t nn = __ballot_sync(0xFFFFFFFFu, nb);
@@ -901,7 +925,28 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
                     mk.N[4 * ry + c] = nn;
                 }
             }
-            if (lane == 0) mk.E[4 * ry + 3] = mk.V[4 * ry + 3] = mk.N[4 * ry + 3] = 0u;
+        }
+        // columns 64..63+2R of 32 / 2R rows at once (lane = row * 2R + column)
+        {
+            constexpr int kCw = 2 * R, kRows = 32 / kCw, kIters = (RH + kRows - 1) / kRows;
+            const int rl = lane / kCw, col = lane - rl * kCw;
+            for (int it = warp; it < kIters; it += kWarps) {
+                const int ry = it * kRows + rl;
+                const bool valid = rl < kRows && ry < RH;
+                bool eb = false, vb = false, nb = false;
+                if (valid) pixel_bits<R, RW, kTrustA>(A, T, sv, iw, ih16, ry, 64 + col, eb, vb, nb);
+                const uint32_t e = __ballot_sync(0xFFFFFFFFu, eb);
+                const uint32_t v = __ballot_sync(0xFFFFFFFFu, vb);
+                const uint32_t nn = __ballot_sync(0xFFFFFFFFu, nb);
+                if (valid && col == 0) {
+                    constexpr uint32_t kM = kCw >= 32 ? 0xFFFFFFFFu : (1u << kCw) - 1u;
+                    const int sh = rl * kCw;
+                    mk.E[4 * ry + 2] = (e >> sh) & kM;
+                    mk.V[4 * ry + 2] = (v >> sh) & kM;
+                    mk.N[4 * ry + 2] = (nn >> sh) & kM;
+                    mk.E[4 * ry + 3] = mk.V[4 * ry + 3] = mk.N[4 * ry + 3] = 0u;
+                }
+            }
         }
         __syncthreads();
         // one thread per region row, 64 output columns at once: hu bit tx <=>
@@ -928,10 +973,11 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
             mk.ni[ry] = in;
         }
         __syncthreads();
-        // one thread per output row: uniform windows (one translation),
-        // interior windows whose rows have at most two runs, interior windows
-        if (threadIdx.x < TH) {
-            const int ty = threadIdx.x;
+        // four threads per output row, 16 columns each: the row's classes
+        // (uniform windows; interior windows whose rows have at most two runs;
+        // the rest, flagged when interior) and its entries of the two lists
+        if (threadIdx.x < 4 * TH) {
+            const int ty = threadIdx.x >> 2, sl = threadIdx.x & 3;
             uint64_t U = mk.hu[ty], T2 = mk.t2[ty], NI = mk.ni[ty];
 #pragma unroll
             for (int k = 1; k <= 2 * R; ++k) {
@@ -939,27 +985,48 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
                 T2 &= mk.t2[ty + k];
                 NI &= mk.ni[ty + k];
             }
-            mk.U[ty] = U;
-            mk.T2[ty] = T2 & NI & ~U;
-            mk.NI[ty] = NI;
+            const uint64_t in = y0 + ty < a.H ? incols : 0ull;
+            U &= in;
+            const uint64_t G = T2 & NI & ~U & in, Tt = ~U & ~G & in;
+            if (sl == 0) mk.U[ty] = U;
+            uint32_t g16 = (uint32_t)(G >> (16 * sl)) & 0xFFFFu;
+            uint32_t t16 = (uint32_t)(Tt >> (16 * sl)) & 0xFFFFu;
+            const uint32_t n16 = (uint32_t)(NI >> (16 * sl));
+            int ng, nt;
+            int og = warp_exclusive_scan(__popc(g16), ng);
+            int ot = warp_exclusive_scan(__popc(t16), nt);
+            int bg = 0, bt = 0;
+            if (lane == 0) {
+                if (ng) bg = atomicAdd(&cnt[3], ng);
+                if (nt) bt = atomicAdd(&cnt[4], nt);
+            }
+            og += __shfl_sync(0xFFFFFFFFu, bg, 0);
+            ot += __shfl_sync(0xFFFFFFFFu, bt, 0);
+            const int k0 = ty * kTW + 16 * sl;
+            while (g16) {
+                const int b = __ffs(g16) - 1;
+                glist[og++] = (uint16_t)(k0 + b);
+                g16 &= g16 - 1u;
+            }
+            while (t16) {
+                const int b = __ffs(t16) - 1;
+                tlist[ot++] = (uint16_t)((k0 + b) | ((n16 >> b) & 1u ? kInteriorFlag : 0));
+                t16 &= t16 - 1u;
+            }
         }
         __syncthreads();
     }
     // output rows: warp w takes rows w, w + 8, ...  A uniform window votes
     // exactly C_S[A(p)] (all its taps share one source position; outside the
-    // source the vote is 0); the other pixels go to two block-wide lists, their
-    // membership read off warp-uniform 64-bit row masks.
+    // source the vote is 0); the other pixels are in the two lists.
     constexpr int kRowsPerWarp = TH / kWarps;
-    const int wcols = min(a.W - x0, kTW);  // columns of the tile inside the target
-    const uint64_t incols = wcols >= 64 ? ~0ull : ((1ull << wcols) - 1ull);
     uint32_t col[kRowsPerWarp][2];
 #pragma unroll
     for (int q = 0; q < kRowsPerWarp; ++q) {
         const int ty = warp + q * kWarps;
-        uint64_t U = ~0ull;
+        uint64_t U;
         if constexpr (R > 0) U = mk.U[ty];
-        if (y0 + ty >= a.H) U = 0;
-        U &= incols;
+        else U = y0 + ty < a.H ? incols : 0ull;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int tx = c * 32 + lane;
@@ -978,10 +1045,9 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
 #pragma unroll
     for (int q = 0; q < kRowsPerWarp; ++q) {
         const int ty = warp + q * kWarps;
-        uint64_t U = ~0ull;
+        uint64_t U;
         if constexpr (R > 0) U = mk.U[ty];
-        if (y0 + ty >= a.H) U = 0;
-        U &= incols;
+        else U = y0 + ty < a.H ? incols : 0ull;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int tx = c * 32 + lane;
@@ -996,45 +1062,6 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
         }
     }
     if constexpr (R > 0) {
-        int *cnt = reinterpret_cast<int *>(smem + L.off_cnt);
-        uint16_t *glist = reinterpret_cast<uint16_t *>(smem + L.off_list0);
-        uint16_t *tlist = reinterpret_cast<uint16_t *>(smem + L.off_list1);
-        uint64_t Gm[kRowsPerWarp], Tm[kRowsPerWarp], Im[kRowsPerWarp];
-        int n_g = 0, n_t = 0;
-#pragma unroll
-        for (int q = 0; q < kRowsPerWarp; ++q) {
-            const int ty = warp + q * kWarps;
-            const uint64_t in = y0 + ty < a.H ? incols : 0ull;
-            Gm[q] = mk.T2[ty] & in;
-            Tm[q] = ~mk.U[ty] & ~mk.T2[ty] & in;
-            Im[q] = mk.NI[ty];
-            n_g += __popcll(Gm[q]);
-            n_t += __popcll(Tm[q]);
-        }
-        int bg = 0, bt = 0;
-        if (lane == 0) {
-            if (n_g) bg = atomicAdd(&cnt[3], n_g);
-            if (n_t) bt = atomicAdd(&cnt[4], n_t);
-        }
-        bg = __shfl_sync(0xFFFFFFFFu, bg, 0);
-        bt = __shfl_sync(0xFFFFFFFFu, bt, 0);
-        const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-        for (int q = 0; q < kRowsPerWarp; ++q) {
-            const int ty = warp + q * kWarps;
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int k = ty * kTW + c * 32 + lane;
-                const uint32_t mg = (uint32_t)(Gm[q] >> (32 * c)), mt = (uint32_t)(Tm[q] >> (32 * c));
-                const uint32_t mi = (uint32_t)(Im[q] >> (32 * c));
-                if ((mg >> lane) & 1u) glist[bg + __popc(mg & lt)] = (uint16_t)k;
-                if ((mt >> lane) & 1u)
-                    tlist[bt + __popc(mt & lt)] = (uint16_t)(k | ((mi >> lane) & 1u ? kInteriorFlag : 0));
-                bg += __popc(mg);
-                bt += __popc(mt);
-            }
-        }
-        __syncthreads();
         vote_two_runs<R, F32, kThreads>(a, sv, T, mk.E, glist, cnt[3], x0, y0);
         vote_taps<R, F32, kThreads>(a, sv, A, T, tlist, cnt[4], x0, y0);
     }
@@ -1181,7 +1208,7 @@ __global__ void __launch_bounds__(Tile<kTH>::Threads) blend_kernel(const FrameAr
         A[i] = inside ? __ldg(a.assign_in + (int64_t)gy * a.W + gx) : kInvalid;
     }
     __syncthreads();
-    vote_tile<R, F32, kTH>(a, L, x0, y0, A, smem);
+    vote_tile<R, F32, kTH, false>(a, L, x0, y0, A, smem);
 }
 
 // Raises a kernel's dynamic shared-memory limit once per (kernel, device);
