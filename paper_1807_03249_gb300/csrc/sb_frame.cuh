@@ -483,11 +483,11 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     const int eager_lo = L_top <= kEagerMinLevel ? 1 : kEagerMinLevel;
     const TileBounds tb = TileBounds::of<R, TH>(rx0, ry0, a.W, a.H);
 
-    // phase 0: every global load (the guide at this thread's seed, the
-    // region's guide, then the seed's table entry) is issued before the
-    // first store that waits on one.  Thread k builds eager cell k (levels
-    // L_top .. eager_lo stacked, each column-major); the level of its cell is
-    // found while counting them.
+    // phase 0: thread k builds eager cell k (levels L_top .. eager_lo
+    // stacked, each column-major; the level of its cell is found while
+    // counting them), then every load of the region's guide is issued before
+    // the first store that waits on one.  Finishing the cell first keeps its
+    // state out of the registers that hold the guide loads.
     int n_eager = 0, my_l = 0, my_ci = 0;
     LevelCells my_g{};
     for (int l = L_top; l >= eager_lo; --l) {
@@ -501,46 +501,72 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
         n_eager += n;
     }
     const bool has_cell = tid < n_eager;
-    CellTask ct{};
-    uint32_t cg = 0;
     if (has_cell) {
-        ct = cell_at(a, my_l, my_ci, my_g);
-        cg = F::load(a.tgt, a.tgt_stride, ct.sx, ct.sy);
+        const CellTask ct = cell_at(a, my_l, my_ci, my_g);
+        const uint32_t cu = seed_source<C, B>(a, F::load(a.tgt, a.tgt_stride, ct.sx, ct.sy));
+        cells[tid] = cell_value(ct, cu, cxo, cyo);
     }
-    // the region's guide, row-major: thread t takes pixels t, t + 256, ...
-    constexpr int NR = RW * RH;
-    constexpr int kIt = (NR + kThreads - 1) / kThreads;
-    constexpr int kStepY = kThreads / RW, kStepX = kThreads % RW;
-    uint32_t gv[kIt];
-    uint32_t inside = 0;  // bit k: pixel tid + k * 256 lies in the target
+    // the region's guide: a warp per region row for columns 0..63 (lanes x
+    // and 32 + x; one row address per lane and row), and the last 2R columns
+    // of 32 / 2R rows at once (lane = row * 2R + column); every load is
+    // issued before the first store
+    constexpr int kWarps = Tile<TH>::Warps;
+    constexpr int kRowIt = (RH + kWarps - 1) / kWarps;
+    constexpr int kCw = R > 0 ? 2 * R : 1, kTRows = 32 / kCw;
+    constexpr int kTailIt = R > 0 ? ((RH + kTRows - 1) / kTRows + kWarps - 1) / kWarps : 0;
+    static_assert(2 * kRowIt + kTailIt <= 32, "inside bits");
+    const int wp = tid >> 5, ln = tid & 31;
+    const int t_rl = ln / kCw, t_col = ln - t_rl * kCw;
+    uint32_t gv[kRowIt][2], gw[kTailIt > 0 ? kTailIt : 1];
+    uint32_t inside = 0;  // bit 2j + c: main pixel (j, c); bit 2 kRowIt + j: tail pixel j
     {
-        int rx = tid % RW, ry = tid / RW;
+        // row address stepped by kWarps rows (only dereferenced inside the target)
+        const uint8_t *row = a.tgt + (int64_t)(ry0 + wp) * a.tgt_stride;
+        const int64_t step = (int64_t)kWarps * a.tgt_stride;
 #pragma unroll
-        for (int k = 0; k < kIt; ++k) {
-            const int gx = rx0 + rx, gy = ry0 + ry;
-            const bool in = (k + 1 < kIt || tid + k * kThreads < NR) && (unsigned)gx < (unsigned)a.W &&
-                            (unsigned)gy < (unsigned)a.H;
-            gv[k] = in ? F::load(a.tgt, a.tgt_stride, gx, gy) : 0u;
-            inside |= (uint32_t)in << k;
-            rx += kStepX;
-            ry += kStepY;
-            if (rx >= RW) {
-                rx -= RW;
-                ++ry;
+        for (int j = 0; j < kRowIt; ++j) {
+            const int ry = wp + j * kWarps, gy = ry0 + ry;
+            const bool rowin = (j + 1 < kRowIt || ry < RH) && (unsigned)gy < (unsigned)a.H;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int gx = rx0 + c * 32 + ln;
+                const bool in = rowin && (unsigned)gx < (unsigned)a.W;
+                gv[j][c] = in ? F::load(row, 0, gx, 0) : 0u;
+                inside |= (uint32_t)in << (2 * j + c);
+            }
+            row += step;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kTailIt; ++j) {
+        const int ry = (wp + j * kWarps) * kTRows + t_rl;
+        const int gx = rx0 + kTW + t_col, gy = ry0 + ry;
+        const bool in = t_rl < kTRows && ry < RH && (unsigned)gx < (unsigned)a.W &&
+                        (unsigned)gy < (unsigned)a.H;
+        gw[j] = in ? F::load(a.tgt, a.tgt_stride, gx, gy) : 0u;
+        inside |= (uint32_t)in << (2 * kRowIt + j);
+    }
+#pragma unroll
+    for (int j = 0; j < kRowIt; ++j) {
+        const int ry = wp + j * kWarps;
+        if (j + 1 < kRowIt || ry < RH) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int i = ry * RW + c * 32 + ln;
+                if ((inside >> (2 * j + c)) & 1u) gt[i] = gv[j][c];
+                else A[i] = kInvalid;
             }
         }
     }
-    uint32_t cu = 0;
-    if (has_cell) cu = seed_source<C, B>(a, cg);
 #pragma unroll
-    for (int k = 0; k < kIt; ++k) {
-        const int i = tid + k * kThreads;
-        if (k + 1 < kIt || i < NR) {
-            if ((inside >> k) & 1u) gt[i] = gv[k];
+    for (int j = 0; j < kTailIt; ++j) {
+        const int ry = (wp + j * kWarps) * kTRows + t_rl;
+        if (t_rl < kTRows && ry < RH) {
+            const int i = ry * RW + kTW + t_col;
+            if ((inside >> (2 * kRowIt + j)) & 1u) gt[i] = gw[j];
             else A[i] = kInvalid;
         }
     }
-    if (has_cell) cells[tid] = cell_value(ct, cu, cxo, cyo);
     if (n_eager > kThreads)
         build_cells<C, B, kThreads>(a, cells, L_top, eager_lo, 0, xa, xb, ya, yb, cxo, cyo, kThreads,
                                     n_eager);
