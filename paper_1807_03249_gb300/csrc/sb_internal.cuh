@@ -113,21 +113,13 @@ struct GuideFmt {
             const uint32_t d = __vabsdiffu4(a, b);
             return __dp4a(d, d, 0u);
         } else if constexpr (C == 1) {
-            uint32_t d = 0;
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                int t = (int)chan(a, c) - (int)chan(b, c);
-                d += (uint32_t)(t * t);
-            }
-            return d;
+            // t^2 < 2^32, so the square modulo 2^32 is exact for either sign
+            const uint32_t t = (a & 0xFFFFu) - (b & 0xFFFFu);
+            return t * t;
         } else {
-            uint64_t d = 0;
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                int64_t t = (int64_t)chan(a, c) - (int64_t)chan(b, c);
-                d += (uint64_t)(t * t);
-            }
-            return d;
+            const int t0 = (int)(a & 0xFFFFu) - (int)(b & 0xFFFFu);
+            const int t1 = (int)(a >> 16) - (int)(b >> 16);
+            return (uint64_t)((int64_t)t0 * t0) + (uint64_t)((int64_t)t1 * t1);
         }
     }
 
