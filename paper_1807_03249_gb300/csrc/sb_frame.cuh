@@ -601,11 +601,16 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
         }
         base += g.ncx * g.ncy;
     }
+    bool synced = false;  // block-uniform
     for (int l = L_top - 1; l >= 1; --l) {
         if (l == kEagerMinLevel - 1 && eager_lo > 1) {
             // levels 2 and 1: the block builds their cells, and only if some
-            // warp still holds a pixel (every thread reaches this point)
-            if (!__syncthreads_or(n_w > 0)) break;
+            // warp still holds a pixel (every thread reaches this point; when
+            // none does, this barrier is also the one that completes A)
+            if (!__syncthreads_or(n_w > 0)) {
+                synced = true;
+                break;
+            }
             build_cells<C, B, kThreads>(a, cells, l, 1, base, xa, xb, ya, yb, cxo, cyo);
             __syncthreads();
         }
@@ -631,7 +636,7 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
         n_w = n_next;
         base += g.ncx * g.ncy;
     }
-    __syncthreads();  // the region's A is complete before the vote reads it
+    if (!synced) __syncthreads();  // the region's A is complete before the vote reads it
 }
 
 // ---------------------------------------------------------------------------
