@@ -138,9 +138,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_counters(workload: str) -> dict:
+def schedule_tag(sched: dict) -> str:
+    return ",".join(f"{k}={int(sched.get(k, 0))}" for k in
+                    ("persistent", "largest_first", "interleave_rows", "tile_rows"))
+
+
+def profiled_counters(workload: str, sched: dict) -> dict:
     """Counters of one batch launch from the committed ncu summary, if it was
-    taken on the current kernel sources (else {})."""
+    taken on the current kernel sources under the same schedule (else {})."""
     path = os.path.join(ROOT, "profiles", f"sb_stylize_batch_{workload}_traffic.txt")
     if not os.path.exists(path):
         return {}
@@ -150,6 +155,8 @@ def profiled_counters(workload: str) -> dict:
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
     if kv.get("kernel_source_hash") != kernel_source_hash():
+        return {}
+    if kv.get("schedule") != schedule_tag(sched):
         return {}
     out = {}
     for k in ("dram_bytes_per_launch", "warp_instructions_per_launch"):
@@ -543,7 +550,7 @@ def run_gpu(args):
     kernel_s = ms_per_step / 1e3  # one batch launch per step
     alg = FRAMES_PER_STEP * ab["frame_bytes"] + ab["exemplar_bytes"]
     achieved = alg / kernel_s / 1e9
-    counters = profiled_counters(args.workload)
+    counters = profiled_counters(args.workload, tuned)
     traffic = counters.get("dram_bytes_per_launch")
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = peaks.get("sm_max_mhz") or 2070.0
@@ -573,8 +580,10 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": f"batch_kernel<{ex.guide.shape[2]},{ex.guide.dtype.itemsize * 8},"
-                                   f"{w.blend_radius}> (sb_stylize_batch)",
+                         "kernel": f"batch_kernel{'_persistent' if tuned.get('persistent') else ''}"
+                                   f"<{ex.guide.shape[2]},{ex.guide.dtype.itemsize * 8},"
+                                   f"{w.blend_radius},{int(tuned.get('tile_rows') or 32)}> "
+                                   f"(sb_stylize_batch)",
                          "peak_source": f"{peak_src} copy bandwidth",
                          "algorithmic_bytes_per_launch": alg,
                          "frame_only_frac": FRAMES_PER_STEP * ab["frame_bytes"] / kernel_s
@@ -790,7 +799,7 @@ def run_workload_4k(dev, steps: int, warmup: int) -> dict:
     hbm = peaks.get("hbm_gbs") or 6800.0
     alg = FRAMES_PER_STEP * ab["frame_bytes"] + ab["exemplar_bytes"]
     achieved = alg / (ms_batch / 1e3) / 1e9
-    counters = profiled_counters("4k")
+    counters = profiled_counters("4k", tuned)
     sm_mhz = peaks.get("sm_max_mhz") or 2070.0
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     issue_peak = sms * 4 * sm_mhz * 1e6
@@ -806,7 +815,9 @@ def run_workload_4k(dev, steps: int, warmup: int) -> dict:
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
                          "traffic": counters.get("dram_bytes_per_launch"),
-                         "kernel": f"batch_kernel<2,16,{w.blend_radius}> (sb_stylize_batch)",
+                         "kernel": f"batch_kernel{'_persistent' if tuned.get('persistent') else ''}"
+                                   f"<2,16,{w.blend_radius},{int(tuned.get('tile_rows') or 32)}> "
+                                   f"(sb_stylize_batch)",
                          "algorithmic_bytes_per_launch": alg,
                          "bytes_rule": "24 frames x (guide in + RGBA8 out) + exemplar "
                                        "(style + guide + table) once per launch"},
