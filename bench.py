@@ -139,8 +139,11 @@ def kernel_source_hash() -> str:
 
 
 def schedule_tag(sched: dict) -> str:
-    return ",".join(f"{k}={int(sched.get(k, 0))}" for k in
-                    ("persistent", "largest_first", "interleave_rows", "tile_rows"))
+    """The schedule as the launch sees it: with rows interleaved every frame
+    has the same tile grid, so largest-first ordering changes nothing."""
+    keys = ("persistent", "interleave_rows", "tile_rows") if sched.get("interleave_rows") else \
+        ("persistent", "largest_first", "interleave_rows", "tile_rows")
+    return ",".join(f"{k}={int(sched.get(k, 0))}" for k in keys)
 
 
 def profiled_counters(workload: str, sched: dict) -> dict:
