@@ -2,20 +2,20 @@
 // coordinate transfer and voting step of Section 3.2.  Templates only; the
 // sb_frame_*.cu files instantiate them per guide format.
 //
-// One CTA owns a 64 x 32 output tile.  The fused kernel computes the
-// assignment A of the tile plus a halo of R pixels (the vote window) in shared
-// memory, so A never reaches device memory:
+// One CTA owns a 64 x TH output tile (TH = 32; the batch kernels also take
+// 16 and 64).  The fused kernel computes the assignment A of the tile plus a
+// halo of R pixels (the vote window) in shared memory, so A never reaches
+// device memory:
 //
-//   phase 0  target guide of the region -> smem (one packed uint32 per pixel,
-//            row-major, thread t loads pixels t, t + 256, ...); the seed cells
-//            of every level >= 3 are built at the same time (levels 2 and 1
-//            have many cells and are built only if a pixel of the tile still
-//            needs them).  A cell is: jitter hash -> seed q clamped into the
-//            target -> G_T[q] -> table entry u*(q).  Cells are stored
-//            column-major (x outer, y inner), each as (-2q, |q|^2) in
-//            region-centred coordinates pre-scaled by 2^11 with the cell's
+//   phase 0  the seed cells of every level >= 3 (thread k builds cell k;
+//            levels 2 and 1 have many cells and are built only if a pixel of
+//            the tile still needs them).  A cell is: jitter hash -> seed q
+//            clamped into the target -> G_T[q] -> table entry u*(q).  Cells
+//            are stored column-major (x outer, y inner), each as (-2q, |q|^2)
+//            in region-centred coordinates pre-scaled by 2^11 with the cell's
 //            column-major index in the low 11 bits, plus the translation
-//            u* - q packed.
+//            u* - q packed.  Then the target guide of the region -> smem (one
+//            packed uint32 per pixel, a warp per region row).
 //   levels   for l = L..1 while pixels are pending: a pixel p takes the
 //            minimum over its 3 x 3 cells of |q|^2 - 2 q.p (which orders seeds
 //            like |q - p|^2) packed with the cell index: one min gives the
@@ -28,15 +28,19 @@
 //            affine in p, so its four keys per cell are one multiply-add and
 //            three adds.  Each warp compacts the segments it rejected into a
 //            list of its own and takes them down the levels by itself.
-//   vote     ballots mark, per region row, where A steps by exactly one pixel
-//            (E, horizontally) and where it continues the row above (V); one
-//            thread per row turns them into 64-bit masks of the output columns
-//            whose window row is one run or at most two runs, one thread per
-//            output row ANDs them over the window.  A window made of one
-//            translation votes exactly C_S[A(p)], a plain copy; a window whose
-//            rows have at most two runs sums one gather per run; the rest
-//            (junctions, frame borders) sum tap by tap.  Integer sums,
-//            round-half-up division.
+//   vote     once A is complete, the region's assignments become style texel
+//            indices (over the dead target guide) and ballots mark, per region
+//            row, where A steps by exactly one pixel (E, horizontally), where
+//            it continues the row above (V) and which assignments lie at least
+//            R pixels inside the source (N).  One thread per region row turns
+//            them into 64-bit masks of the output columns whose window row is
+//            one run, at most two runs, or interior (over the dead seed
+//            cells); four threads per output row AND them over the window and
+//            list the row's pixels by class.  A window made of one translation
+//            votes exactly C_S[A(p)], a plain copy; an interior window whose
+//            rows have at most two runs sums one gather per run with no source
+//            test; the rest (junctions, frame and source borders) sum tap by
+//            tap.  Integer sums, round-half-up division.
 //   store    uniform windows store from the copy pass (coalesced rows), the
 //            others from the two list passes.
 #pragma once
