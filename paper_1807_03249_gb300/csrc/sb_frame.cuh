@@ -8,8 +8,9 @@
 // device memory:
 //
 //   phase 0  the seed cells of every level >= 3 (thread k builds cell k;
-//            levels 2 and 1 have many cells and are built only if a pixel of
-//            the tile still needs them).  A cell is: jitter hash -> seed q
+//            level 2 has many cells and is built only if a pixel of the tile
+//            still needs it; level 1 has no cell table, its few pixels search
+//            their seeds one by one).  A cell is: jitter hash -> seed q
 //            clamped into the target -> G_T[q] -> table entry u*(q).  Cells
 //            are stored column-major (x outer, y inner), each as (-2q, |q|^2)
 //            in region-centred coordinates pre-scaled by 2^11 with the cell's
@@ -27,7 +28,10 @@
 //            lane: a segment lies in one cell at levels >= 2 and the keys are
 //            affine in p, so its four keys per cell are one multiply-add and
 //            three adds.  Each warp compacts the segments it rejected into a
-//            list of its own and takes them down the levels by itself.
+//            list of its own and takes them down the levels by itself.  The
+//            level lists and, later, the vote's two pixel lists share one
+//            area, and level 1 keeps no cells, so four CTAs leave most of the
+//            SM's unified L1 / shared memory to the L1 cache.
 //   vote     once A is complete, the region's assignments become style texel
 //            indices (over the dead target guide) and ballots mark, per region
 //            row, where A steps by exactly one pixel (E, horizontally), where
@@ -105,8 +109,27 @@ __host__ __device__ constexpr int cells_bound(int RW, int RH, int l) {
 
 struct SmemLayout {
     int RW, RH, NR, NC;
-    size_t off_cells, off_gt, off_A, off_list0, off_list1, off_bytes, off_masks, off_cnt, total;
+    size_t off_cells, off_gt, off_A, off_lists, off_bytes, off_masks, off_cnt, total;
 };
+
+// Rows above the tile where the first segment (4 rows, starting at a target row
+// that is a multiple of 4) starts: the blend radius rounded up to 4.
+__host__ __device__ constexpr int seg_pad(int r) { return (r + 3) / 4 * 4; }
+
+// Entries of one warp's pending-segment list: the most segments a warp takes
+// at the top level (segments of 4 rows cover the region and the seg_pad rows
+// above and below the tile).
+__host__ __device__ constexpr int warp_list_cap(int r, int th) {
+    return ((kTW + 2 * r) * ((th + 2 * seg_pad(r)) / 4) + 8 * th - 1) / (8 * th) * 32;
+}
+
+// Entries of the list area: during the assignment, two pending lists per
+// warp (this level's and the next one's); during the vote, the tile's two
+// pixel lists, whose classes are disjoint, one from each end.
+__host__ __device__ constexpr int list_entries(int r, int th) {
+    return 2 * (th / 4) * warp_list_cap(r, th) > th * kTW ? 2 * (th / 4) * warp_list_cap(r, th)
+                                                           : th * kTW;
+}
 
 // Bytes of the vote's masks: per region row E, V, N (4 words each) and the
 // 64-bit output-column masks hu, t2, vc, ni; per output row U, T2, NI.
@@ -118,7 +141,11 @@ __host__ __device__ constexpr size_t vote_mask_bytes(int r, int th) {
 // the region's target guide are dead: the vote lays its masks over the cells
 // (the area is at least as large as the masks) and the source texel index of
 // each region pixel's assignment over the guide.  The level bytes exist only
-// for the assignment-only kernel (the fused path never stores levels).
+// for the assignment-only kernel (the fused path never stores levels).  Cells
+// are kept for levels 2 and up (level 1 searches its seeds pixel by pixel), and
+// one list area serves both the level loop and the vote.  The smaller the four
+// CTAs' shared memory, the more of the SM's unified L1 / shared-memory array
+// is left to the L1 cache that serves the exemplar gathers.
 __host__ __device__ inline SmemLayout smem_layout(int r, int levels, bool level_bytes = false,
                                                   int th = kTH) {
     SmemLayout s;
@@ -126,7 +153,7 @@ __host__ __device__ inline SmemLayout smem_layout(int r, int levels, bool level_
     s.RH = th + 2 * r;
     s.NR = s.RW * s.RH;
     s.NC = 0;
-    for (int l = 1; l <= levels; ++l) s.NC += cells_bound(s.RW, s.RH, l);
+    for (int l = 2; l <= levels; ++l) s.NC += cells_bound(s.RW, s.RH, l);
     size_t o = 0;
     s.off_cells = o;
     s.off_masks = o;
@@ -136,10 +163,8 @@ __host__ __device__ inline SmemLayout smem_layout(int r, int levels, bool level_
     o += sizeof(uint32_t) * (size_t)s.NR;
     s.off_A = o;
     o += sizeof(uint32_t) * (size_t)s.NR;
-    s.off_list0 = o;
-    o += sizeof(uint16_t) * (size_t)s.NR;
-    s.off_list1 = o;
-    o += sizeof(uint16_t) * (size_t)s.NR;
+    s.off_lists = o;
+    o += sizeof(uint16_t) * (size_t)list_entries(r, th);
     s.off_bytes = o;
     if (level_bytes) o += (size_t)s.NR;
     o = (o + 15) & ~(size_t)15;
@@ -273,7 +298,7 @@ __device__ __forceinline__ void build_cells(const FrameArgs &a, int4 *cells, int
 // >= 2 a segment lies inside one seed cell.
 template <int R, int TH>
 struct Segs {
-    static constexpr int kPad = (R + 3) / 4 * 4;  // first segment row: kPad rows above the tile
+    static constexpr int kPad = seg_pad(R);  // first segment row: kPad rows above the tile
     static constexpr int RW = kTW + 2 * R, RH = TH + 2 * R;
     static constexpr int NSY = (TH + 2 * kPad) / 4;
     static constexpr int NS = RW * NSY;
@@ -350,10 +375,53 @@ __device__ __forceinline__ uint32_t test_segment(const SrcView &a, const uint32_
     return rej;
 }
 
-// Levels where every pixel searches its own seed: level 1 (a segment spans
-// two cells) and the levels above kPackedMaxLevel (keys are 64-bit squared
-// distances packed with the cell index).  Both are rare, so pixels go one at
-// a time with little live state (the common path keeps its registers).
+// Level 1 (seed spacing 2; a segment spans two cells), pixel by pixel and
+// without a cell table: each pixel hashes its own 3 x 3 seed cells, keeps the
+// nearest seed in NearestSeed's order (x outer, y inner, first minimum), looks
+// the seed's guide up (table or search index) and takes the candidate clamped
+// into the source: the finest level accepts every pixel.  Few pixels reach
+// level 1, so a table of the region's level-1 cells would cost more shared
+// memory than building it saves.  It runs in a pass of its own after the
+// other levels (its state stays out of the registers of their loops).
+template <int C, int B, int R, int TH>
+__device__ __forceinline__ void segment_level1(const FrameArgs &a, uint32_t *A, uint8_t *lev,
+                                               int rx0, int ry0, int rx, int ry, uint32_t m) {
+    using F = GuideFmt<C, B>;
+    constexpr int RW = Segs<R, TH>::RW;
+    const uint32_t lk = level_key(a.seed, 1);
+    const int px = rx0 + rx;
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+        if (!((m >> j) & 1u)) continue;
+        const int py = ry0 + ry + j;
+        int best = INT_MAX, qx = 0, qy = 0;
+#pragma unroll 1
+        for (int d = 0; d < 9; ++d) {
+            const int bx = (px >> 1) + d / 3 - 1, by = (py >> 1) + d % 3 - 1;
+            const uint32_t h = cell_hash(lk, bx, by);
+            // offsets floor(2 j) of the 16-bit jitter fractions
+            const int sx = min(max(2 * bx + (int)((h & 0xFFFFu) >> 15), 0), a.W - 1);
+            const int sy = min(max(2 * by + (int)(h >> 31), 0), a.H - 1);
+            const int dist = (sx - px) * (sx - px) + (sy - py) * (sy - py);
+            if (dist < best) {
+                best = dist;
+                qx = sx;
+                qy = sy;
+            }
+        }
+        const uint32_t u = seed_source<C, B>(a, F::load(a.tgt, a.tgt_stride, qx, qy));
+        const int sx = min(max((int)(u & 0xFFFFu) + px - qx, 0), a.Ws - 1);
+        const int sy = min(max((int)(u >> 16) + py - qy, 0), a.Hs - 1);
+        const int i = (ry + j) * RW + rx;
+        A[i] = (uint32_t)sx | ((uint32_t)sy << 16);
+        if (lev) lev[i] = 1;
+    }
+}
+
+// Levels above kPackedMaxLevel, where every pixel searches its own seed (keys
+// are 64-bit squared distances packed with the cell index).  They are rare,
+// so pixels go one at a time with little live state (the common path keeps
+// its registers).
 template <int C, int B, int R, int TH>
 __device__ __forceinline__ uint32_t segment_level_rare(const SrcView &a, const uint32_t *gt,
                                                        uint32_t *A, uint8_t *lev,
@@ -364,45 +432,29 @@ __device__ __forceinline__ uint32_t segment_level_rare(const SrcView &a, const u
     constexpr int RW = Segs<R, TH>::RW, RH = Segs<R, TH>::RH;
     constexpr int kMask = (1 << kKeyShift) - 1;
     const int prx = rx - RW / 2, pry = ry - RH / 2;
-    const bool packed = l <= kPackedMaxLevel;
     uint32_t rej = 0;
 #pragma unroll 1
     for (int j = 0; j < 4; ++j) {
         if (!((m >> j) & 1u)) continue;
-        // level 1: rows 0-1 and 2-3 lie in consecutive cells of one column
-        const int cj = c0 + (l == 1 ? (j >> 1) : 0);
         long long key = LLONG_MAX;
 #pragma unroll 1
         for (int d = 0; d < 9; ++d) {
-            const int c = cj + (d / 3 - 1) * ncy + (d % 3 - 1);
+            const int c = c0 + (d / 3 - 1) * ncy + (d % 3 - 1);
             const int4 cl = cells[c];
-            if (packed) {
-                // packed cells carry the index in their low bits already
-                key = min(key, (long long)(int)((uint32_t)cl.z + (uint32_t)cl.x * (uint32_t)prx +
-                                                (uint32_t)cl.y * (uint32_t)(pry + j)));
-            } else {
-                const long long dx = prx + cl.x, dy = pry + j + cl.y;
-                key = min(key, ((dx * dx + dy * dy) << kKeyShift) | (c - base));
-            }
+            const long long dx = prx + cl.x, dy = pry + j + cl.y;
+            key = min(key, ((dx * dx + dy * dy) << kKeyShift) | (c - base));
         }
+        // these cells hold u* and -q
         const int4 cl = cells[base + (int)(key & kMask)];
-        // packed cells: translation u* - q (biased); the others: u* and -q
-        const int ox = packed ? -kShiftBias : cl.x, oy = packed ? -kShiftBias : cl.y;
-        int sx = (int)((uint32_t)cl.w & 0xFFFFu) + prx + ox;
-        int sy = (int)((uint32_t)cl.w >> 16) + pry + j + oy;
+        const int sx = (int)((uint32_t)cl.w & 0xFFFFu) + prx + cl.x;
+        const int sy = (int)((uint32_t)cl.w >> 16) + pry + j + cl.y;
         const int i = (ry + j) * RW + rx;
-        bool acc = true;
-        if (l == 1) {
-            sx = min(max(sx, 0), a.Ws - 1);
-            sy = min(max(sy, 0), a.Hs - 1);
-        } else {
-            acc = (unsigned)sx < (unsigned)a.Ws && (unsigned)sy < (unsigned)a.Hs;
-            if (acc) {
-                const uint64_t d = F::dist(
-                    __ldg(a.src_packed + ((uint32_t)sy * (uint32_t)a.Ws + (uint32_t)sx)), gt[i]);
-                if constexpr (B == 8) acc = (uint32_t)d <= t32;
-                else acc = d <= a.threshold;
-            }
+        bool acc = (unsigned)sx < (unsigned)a.Ws && (unsigned)sy < (unsigned)a.Hs;
+        if (acc) {
+            const uint64_t d = F::dist(
+                __ldg(a.src_packed + ((uint32_t)sy * (uint32_t)a.Ws + (uint32_t)sx)), gt[i]);
+            if constexpr (B == 8) acc = (uint32_t)d <= t32;
+            else acc = d <= a.threshold;
         }
         if (acc) {
             A[i] = (uint32_t)sx | ((uint32_t)sy << 16);
@@ -414,12 +466,12 @@ __device__ __forceinline__ uint32_t segment_level_rare(const SrcView &a, const u
     return rej;
 }
 
-// Level l (1 <= l <= kMaxLevels) of the pixels m of the segment at
+// Level l (2 <= l <= kMaxLevels) of the pixels m of the segment at
 // region (rx, ry): returns the rejected ones.  The packed keys of the nine
 // candidates are affine in p, so the pixels that pick a given seed form a
 // convex set: when the first and last pixel of m pick the same seed, every
 // pixel between them does and the nine-way search runs once.  Otherwise each
-// pixel searches (level 1 and the unscaled levels: segment_level_rare).
+// pixel searches (the unscaled levels: segment_level_rare).
 template <int C, int B, int R, int TH>
 __device__ __forceinline__ uint32_t segment_level(const FrameArgs &a, const uint32_t *gt,
                                                   uint32_t *A, uint8_t *lev, const int4 *cells,
@@ -433,7 +485,7 @@ __device__ __forceinline__ uint32_t segment_level(const FrameArgs &a, const uint
     const int c0 = base + (((rx0 + rx) >> l) - g.cx0) * g.ncy + (((ry0 + ry) >> l) - g.cy0);
     const int ibase = ry * RW + rx;
     const SrcView sv{a.src_packed, a.Ws, a.Hs, a.threshold};
-    if (l == 1 || l > kPackedMaxLevel)
+    if (l > kPackedMaxLevel)
         return segment_level_rare<C, B, R, TH>(sv, gt, A, lev, cells, base, c0, g.ncy, l, t32, rx, ry,
                                            m);
     // every lane evaluates the nine keys at all four pixels (three adds per
@@ -475,8 +527,7 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     int4 *cells = reinterpret_cast<int4 *>(smem + L.off_cells);
     uint32_t *gt = reinterpret_cast<uint32_t *>(smem + L.off_gt);
     uint32_t *A = reinterpret_cast<uint32_t *>(smem + L.off_A);
-    uint16_t *const list0 = reinterpret_cast<uint16_t *>(smem + L.off_list0);
-    uint16_t *const list1 = reinterpret_cast<uint16_t *>(smem + L.off_list1);
+    uint16_t *const lists = reinterpret_cast<uint16_t *>(smem + L.off_lists);
     const int tid = threadIdx.x;
 
     const int xa = max(rx0, 0), xb = min(rx0 + RW, a.W) - 1;
@@ -484,7 +535,8 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     const int cxo = rx0 + RW / 2, cyo = ry0 + RH / 2;
     const uint32_t t32 = a.threshold > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)a.threshold;
     const int L_top = a.levels;
-    const int eager_lo = L_top <= kEagerMinLevel ? 1 : kEagerMinLevel;
+    // levels with a cell table: L_top down to 2 (level 1 has none)
+    const int eager_lo = L_top <= kEagerMinLevel ? 2 : kEagerMinLevel;
     const TileBounds tb = TileBounds::of<R, TH>(rx0, ry0, a.W, a.H);
 
     // phase 0: thread k builds eager cell k (levels L_top .. eager_lo
@@ -581,22 +633,24 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
     // round); every warp keeps the segments it rejected (entries: segment
     // index << 4 | pixel mask) in a list of its own and takes them down the
     // eager levels by itself, compacting with ballots: no block barrier and no
-    // shared counter between those levels.  Levels 2 and 1 need their cells
-    // built by the whole block first, and only if some warp still holds a
-    // pixel.
+    // shared counter between those levels.  Level 2 needs its cells built by
+    // the whole block first, and only if some warp still holds a pixel; level
+    // 1 goes pixel by pixel without cells.
     using S = Segs<R, TH>;
-    constexpr int kWarpCap = (S::NS + kThreads - 1) / kThreads * 32;
+    constexpr int kWarpCap = warp_list_cap(R, TH);
+    static_assert(kWarpCap == (S::NS + kThreads - 1) / kThreads * 32, "list capacity");
     const int warp = tid >> 5, lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
-    uint16_t *wl_cur = list0 + warp * kWarpCap, *wl_nxt = list1 + warp * kWarpCap;
+    uint16_t *wl_cur = lists + warp * kWarpCap, *wl_nxt = lists + (kWarps + warp) * kWarpCap;
     int n_w = 0, base = 0;
     {
         const LevelCells g = level_cells(L_top, xa, xb, ya, yb);
         for (int s0 = 0; s0 < S::NS; s0 += kThreads) {
             const int sg = s0 + tid;
             const uint32_t m = sg < S::NS ? tb.template mask<R, TH>(S::rx(sg), S::ry(sg)) : 0u;
-            uint32_t rej = 0;
-            if (m)
+            // a hierarchy of one level leaves every pixel to the level-1 pass
+            uint32_t rej = L_top == 1 ? m : 0u;
+            if (m && L_top > 1)
                 rej = segment_level<C, B, R, TH>(a, gt, A, lev, cells, base, g, L_top, rx0, ry0,
                                                  t32, S::rx(sg), S::ry(sg), m);
             const unsigned mk = __ballot_sync(0xFFFFFFFFu, rej != 0);
@@ -606,16 +660,16 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
         base += g.ncx * g.ncy;
     }
     bool synced = false;  // block-uniform
-    for (int l = L_top - 1; l >= 1; --l) {
-        if (l == kEagerMinLevel - 1 && eager_lo > 1) {
-            // levels 2 and 1: the block builds their cells, and only if some
-            // warp still holds a pixel (every thread reaches this point; when
-            // none does, this barrier is also the one that completes A)
+    for (int l = L_top - 1; l >= 2; --l) {
+        if (l == kEagerMinLevel - 1 && eager_lo > 2) {
+            // level 2: the block builds its cells, and only if some warp
+            // still holds a pixel (every thread reaches this point; when none
+            // does, this barrier is also the one that completes A)
             if (!__syncthreads_or(n_w > 0)) {
                 synced = true;
                 break;
             }
-            build_cells<C, B, kThreads>(a, cells, l, 1, base, xa, xb, ya, yb, cxo, cyo);
+            build_cells<C, B, kThreads>(a, cells, 2, 2, base, xa, xb, ya, yb, cxo, cyo);
             __syncthreads();
         }
         const LevelCells g = level_cells(l, xa, xb, ya, yb);
@@ -639,6 +693,12 @@ __device__ __forceinline__ void assign_region(const FrameArgs &a, const SmemLayo
         wl_nxt = t;
         n_w = n_next;
         base += g.ncx * g.ncy;
+    }
+    // level 1: the pixels still pending, each warp its own list
+    for (int j0 = 0; j0 < n_w; j0 += 32) {
+        const uint32_t e = j0 + lane < n_w ? wl_cur[j0 + lane] : 0u;
+        const int sg = (int)(e >> 4);
+        if (e & 15u) segment_level1<C, B, R, TH>(a, A, lev, rx0, ry0, S::rx(sg), S::ry(sg), e & 15u);
     }
     if (!synced) __syncthreads();  // the region's A is complete before the vote reads it
 }
@@ -816,8 +876,9 @@ __device__ __forceinline__ void vote_two_runs(const FrameArgs &a, const StyleVie
 
 // Every other window (junctions of three or more chunks, frame borders and
 // taps near the source border): tap by tap.  The block's such pixels share
-// one list; an entry's top bit marks a window whose taps all come from
-// interior assignments, which skips the per-tap source test.
+// one list, stored downwards from `list` (entry j at list[-j]); an entry's top
+// bit marks a window whose taps all come from interior assignments, which
+// skips the per-tap source test.
 constexpr uint16_t kInteriorFlag = 0x8000u;
 
 template <int R, bool F32, int NT>
@@ -830,7 +891,7 @@ __device__ __forceinline__ void vote_taps(const FrameArgs &a, const StyleView &s
     constexpr int kUnroll = R <= 7 ? 2 * R + 1 : 1;
     const uint32_t S = sv.stride;
     for (int j = threadIdx.x; j < n; j += NT) {
-        const int e = list[j];
+        const int e = list[-j];  // the list runs downwards
         const int k = e & ~(int)kInteriorFlag;
         const int tx = k % kTW, ty = k / kTW;
         VoteAcc<kPacked> acc;
@@ -931,8 +992,11 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
     const VoteMasks<R, TH> mk = VoteMasks<R, TH>::at(smem + L.off_masks);
     uint32_t *const T = reinterpret_cast<uint32_t *>(smem + L.off_gt);
     int *const cnt = reinterpret_cast<int *>(smem + L.off_cnt);
-    uint16_t *const glist = reinterpret_cast<uint16_t *>(smem + L.off_list0);
-    uint16_t *const tlist = reinterpret_cast<uint16_t *>(smem + L.off_list1);
+    // the two pixel lists share one area: two-run windows from its start,
+    // tap-by-tap windows downwards from entry 64 TH - 1 (the classes are
+    // disjoint, so together they hold at most the tile's 64 TH pixels)
+    uint16_t *const glist = reinterpret_cast<uint16_t *>(smem + L.off_lists);
+    uint16_t *const tlist = glist + (kTW * TH - 1);
     const int wcols = min(a.W - x0, kTW);  // columns of the tile inside the target
     const uint64_t incols = wcols >= 64 ? ~0ull : ((1ull << wcols) - 1ull);
     if (R > 0 && threadIdx.x == 0) cnt[3] = cnt[4] = 0;  // two-runs and tap-by-tap list lengths
@@ -1045,7 +1109,7 @@ __device__ __forceinline__ void vote_tile(const FrameArgs &a, const SmemLayout &
             }
             while (t16) {
                 const int b = __ffs(t16) - 1;
-                tlist[ot++] = (uint16_t)((k0 + b) | ((n16 >> b) & 1u ? kInteriorFlag : 0));
+                tlist[-(ot++)] = (uint16_t)((k0 + b) | ((n16 >> b) & 1u ? kInteriorFlag : 0));
                 t16 &= t16 - 1u;
             }
         }
@@ -1168,23 +1232,29 @@ struct BatchArgs {
 template <int C, int B, int R, int TH>
 __device__ __forceinline__ void batch_tile(const BatchArgs &b, const SmemLayout &L, int t,
                                            unsigned char *smem) {
+    // the tile's frame k and position, then one inlined tile body for both
+    // orders (two would double the kernel's code and its register pressure)
+    int k, tx, ty;
     if (b.rows_interleaved) {
         const int per_row = b.n * b.rows_tx;
-        const int r = t / per_row, rem = t - r * per_row;
-        const int k = rem / b.rows_tx;
-        const FrameArgs a = b.f[k];
-        frame_tile<C, B, kStylize, R, TH>(a, L, rem - k * b.rows_tx, r, smem);
-        return;
+        ty = t / per_row;
+        const int rem = t - ty * per_row;
+        k = rem / b.rows_tx;
+        tx = rem - k * b.rows_tx;
+    } else {
+        int lo = 0, hi = b.n - 1;  // last frame whose first tile is <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.tile_start[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        k = lo;
+        const int lt = t - b.tile_start[k];
+        ty = lt / b.tiles_x[k];
+        tx = lt - ty * b.tiles_x[k];
     }
-    int lo = 0, hi = b.n - 1;  // last frame whose first tile is <= t
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (b.tile_start[mid] <= t) lo = mid;
-        else hi = mid - 1;
-    }
-    const FrameArgs a = b.f[lo];  // register copy: field reads become plain operands
-    const int lt = t - b.tile_start[lo];
-    frame_tile<C, B, kStylize, R, TH>(a, L, lt % b.tiles_x[lo], lt / b.tiles_x[lo], smem);
+    const FrameArgs a = b.f[k];  // register copy: field reads become plain operands
+    frame_tile<C, B, kStylize, R, TH>(a, L, tx, ty, smem);
 }
 
 template <int C, int B, int R, int TH>
