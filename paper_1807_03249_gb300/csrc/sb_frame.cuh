@@ -1214,6 +1214,25 @@ __global__ void __launch_bounds__(Tile<kTH>::Threads, min_ctas(R))
 // while the last tiles of earlier frames finish.
 constexpr int kMaxBatch = 128;
 
+// floor(n / d) for 0 <= n < 2^31 and 1 <= d < 2^31 by one widening multiply:
+// with l = ceil(log2 d) and m = ceil(2^(31 + l) / d), floor(n / d) =
+// floor(n m / 2^(31 + l)) for every such n (Granlund and Montgomery, "Division
+// by invariant integers using multiplication", PLDI 1994, Theorem 4.2: m d -
+// 2^(31 + l) < d <= 2^l).  m has at most 33 bits, so n m fits 64 bits.
+struct FastDiv {
+    uint64_t m;
+    uint32_t shift;  // 31 + l
+    static FastDiv of(uint32_t d) {
+        uint32_t l = 0;
+        while ((1ull << l) < d) ++l;
+        const uint32_t sh = 31 + l;
+        return FastDiv{((1ull << sh) + d - 1) / d, sh};
+    }
+    __device__ __forceinline__ int operator()(int n) const {
+        return (int)(((uint64_t)(uint32_t)n * m) >> shift);
+    }
+};
+
 struct BatchArgs {
     int n;
     // tile order: 0 frame by frame; otherwise (every frame has rows_tx x
@@ -1221,8 +1240,11 @@ struct BatchArgs {
     // exemplar lines those rows gather stay in L2 across the frames
     int rows_interleaved;
     int rows_tx;
+    FastDiv div_row;      // by n * rows_tx, the tiles of one interleaved tile row
+    FastDiv div_rows_tx;  // by rows_tx
     int tile_start[kMaxBatch + 1];
     int tiles_x[kMaxBatch];
+    FastDiv div_tiles_x[kMaxBatch];
     FrameArgs f[kMaxBatch];
 };
 
@@ -1236,10 +1258,9 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &b, const SmemLayout 
     // orders (two would double the kernel's code and its register pressure)
     int k, tx, ty;
     if (b.rows_interleaved) {
-        const int per_row = b.n * b.rows_tx;
-        ty = t / per_row;
-        const int rem = t - ty * per_row;
-        k = rem / b.rows_tx;
+        ty = b.div_row(t);
+        const int rem = t - ty * (b.n * b.rows_tx);
+        k = b.div_rows_tx(rem);
         tx = rem - k * b.rows_tx;
     } else {
         int lo = 0, hi = b.n - 1;  // last frame whose first tile is <= t
@@ -1250,7 +1271,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs &b, const SmemLayout 
         }
         k = lo;
         const int lt = t - b.tile_start[k];
-        ty = lt / b.tiles_x[k];
+        ty = b.div_tiles_x[k](lt);
         tx = lt - ty * b.tiles_x[k];
     }
     const FrameArgs a = b.f[k];  // register copy: field reads become plain operands

@@ -324,6 +324,7 @@ static sb_status prepare_batch(const sb_frame *frames, int32_t n_frames, int32_t
         if (next > INT_MAX) return fail(SB_ERR_INVALID_ARG, "sb_stylize_batch: too many tiles");
         b.tile_start[i + 1] = (int)next;
         b.tiles_x[i] = max(1, (f.tgt_guide.width + kTW - 1) / kTW);
+        b.div_tiles_x[i] = FastDiv::of((uint32_t)b.tiles_x[i]);
         FrameArgs a = frame_args(&f.tgt_guide, f.lut, f.levels, f.threshold, f.seed);
         a.style = f.src_style.data;
         a.style_stride_px = (int)(f.src_style.row_stride / 4);
@@ -342,6 +343,8 @@ static sb_status prepare_batch(const sb_frame *frames, int32_t n_frames, int32_t
         if (same) {
             b.rows_interleaved = 1;
             b.rows_tx = tx0;
+            b.div_row = FastDiv::of((uint32_t)(n_frames * tx0));
+            b.div_rows_tx = FastDiv::of((uint32_t)tx0);
         }
     }
     int dev = 0;
