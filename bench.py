@@ -61,6 +61,9 @@ def _args():
                    help="build the step's frames and launch sb_stylize_batch twice, then "
                         "sb_lookup_only_batch twice, no timing (a fixed launch sequence for ncu "
                         "captures)")
+    p.add_argument("--single-frames", type=int, default=0,
+                   help="with --profile-once: then this many sb_stylize calls, one per frame of the "
+                        "step (the single-frame path), before the lookup-only launches")
     p.add_argument("--schedule", default="0,0,0,0",
                    help="with --profile-once: the batch schedule as persistent,largest_first,"
                         "interleave_rows,tile_rows (the bench line's config.schedule)")
@@ -1024,11 +1027,17 @@ def profile_once(args):
     sched = {"persistent": pers, "largest_first": lf, "interleave_rows": il, "tile_rows": rows}
     for _ in range(2):
         sb.stylize_batch(batch, w.blend_radius, schedule=sched)
+    # then, if asked, the single-frame path: one sb_stylize per frame
+    for i in range(min(args.single_frames, len(batch))):
+        f = batch[i]
+        sb.stylize(f.tgt_guide, gs, st, lut, w.levels, w.threshold, w.blend_radius, f.seed,
+                   out=f.out)
     # then the lookup-only comparator over the same frames, batched, twice
     for _ in range(2):
         sb.lookup_only_batch(batch)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_once": w.name, "frames": len(batch), "schedule": sched}))
+    print(json.dumps({"profile_once": w.name, "frames": len(batch), "schedule": sched,
+                      "single_frames": min(args.single_frames, len(batch))}))
 
 
 def main():
